@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Throughput of one RPMD time step (B300, sm_103a) on synthetic flexible water.
+
+Default workload: 4,096 q-SPC/Fw-style waters (12,288 atoms, 49.7 A box, rc 9 A),
+P = 32 beads, 300 K, dt 0.5 fs, PILE thermostat, mixed precision (FP32 pair
+math, int64 fixed-point forces, FP64 modes and integrator).
+
+A "step" is one full BAOAB step of the hot path: B-A-O-A in normal modes with
+the bead transform, the centroid-list check (and rebuild when due), the
+nonbonded and bonded bead forces, the force projection and the closing B.
+Each timed step is bracketed by CUDA events on the library's stream; the L2 is
+flushed (a 256 MB write) between steps, outside the events.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+Under torchrun every rank runs an independent replica (the path is replicas
+only on one-GPU machines); rank 0 prints the line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom·bead·steps/s (ns/day) RPMD & adQTB water vs FP64 GPU path at stated error"
+UNIT = "atom·bead·steps/s"
+# Algorithmic FP32 flops per in-cutoff bead pair (FMA = 2) of the DSF Coulomb force on both
+# atoms, and the extra flops of the LJ term on O-O pairs.
+FLOPS_PAIR = 45
+FLOPS_LJ = 8
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[2 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _config(name):
+    from paper_2212_03137_b300.workloads import CONFIGS
+    return CONFIGS[name]
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2212_03137_b300 import build, qhp
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = _config(args.workload)
+    sysobj = qhp.System.from_config(cfg, seed=cfg.seed + 1000 * rank)
+    h = sysobj.h
+    # one explicit stream for the library's kernels, the L2 flush and the timing events
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    qhp.qhp_set_stream(h, stream.cuda_stream)
+    N, P = sysobj.n_atoms, sysobj.P
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    step = qhp.qhp_step_adqtb if cfg.thermostat == "adqtb" else qhp.qhp_step_rpmd
+
+    # warm-up (compiles the step graph, fills the list)
+    for _ in range(args.warmup):
+        step(h, 1)
+    qhp.qhp_sync(h)
+    pairs, oo_pairs = qhp.qhp_count_pairs(h)
+    qhp.qhp_set_profiling(h, True)
+    step(h, 1)
+    qhp.qhp_sync(h)
+
+    dist = ws > 1
+    if dist:
+        import torch.distributed as td
+        td.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = qhp.qhp_get_info(h).kernel_launches
+    step_ms, pair_ms = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                       # evict L2 between timed steps (outside the events)
+            e0.record(stream)
+            step(h, 1)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            pair_ms.append(qhp.qhp_get_profile(h).pair_ms)
+    launches = qhp.qhp_get_info(h).kernel_launches - launches0
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        import torch.distributed as td
+        t = torch.tensor([total_ms], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        total_ms = float(t.item())
+        td.barrier()
+    qhp.qhp_set_profiling(h, False)
+
+    units = N * P * args.steps * ws
+    value = units / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+    steps_per_s = 1e3 / ms_per_step
+    ns_day = steps_per_s * cfg.dt_fs * 86400.0 / 1e6
+
+    out = None
+    if rank == 0:
+        peaks, src = _peaks()
+        clocks = clk.summary()
+        smax = float(peaks.get("sm_max_mhz", 2032.0))
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_tflops = n_sm * 128 * 2 * smax * 1e6 / 1e12
+        flops_launch = FLOPS_PAIR * pairs + FLOPS_LJ * oo_pairs
+        mean_pair_ms = float(np.mean(pair_ms))
+        achieved = flops_launch / (mean_pair_ms * 1e-3) / 1e12
+        traffic = _profile_traffic("pair", args.workload)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/i64/f64 (mixed)", "data": "synthetic",
+            "ns_per_day": ns_day,
+            "config": {"workload": args.workload, "n_molecules": cfg.n_mol, "n_atoms": N, "beads": P,
+                       "box_A": cfg.box, "rc_A": cfg.rc, "skin_A": cfg.skin, "dt_fs": cfg.dt_fs,
+                       "temperature_K": cfg.temperature, "thermostat": cfg.thermostat, "precision": cfg.precision,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "roofline": {"kernel": "nonbonded pair kernel", "bound": "alu", "achieved": achieved,
+                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": traffic, "pairs_per_launch": pairs, "oo_pairs_per_launch": oo_pairs,
+                         "flops_per_launch": flops_launch, "mean_launch_ms": mean_pair_ms,
+                         "share_of_step": mean_pair_ms / ms_per_step,
+                         "peak_source": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} clock)"},
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+    if args.e2e:
+        e2e = _e2e(args, h, N, P, step, dev, ws)
+        if rank == 0:
+            out["e2e"] = e2e
+    if args.fp64 and rank == 0:
+        out["fp64_gpu_path"] = _fp64_path(args, cfg, dev)
+        out["speedup_vs_fp64_gpu_path"] = value / ws / out["fp64_gpu_path"]["value"]
+    sysobj.close()
+    if rank == 0 and args.cpu_baseline:
+        cb, err = _cpu_baseline(cfg, args)
+        out["cpu_baseline"] = cb
+        if err is not None:
+            out["force_error_rms_rel_vs_oracle"] = err
+    return out
+
+
+def _e2e(args, h, N, P, step, dev, ws):
+    """Public API with host buffers: per step upload the momenta (pinned), step, read back the centroids."""
+    import torch
+    from paper_2212_03137_b300 import qhp
+    Q, Pm = qhp.qhp_get_modes(h)
+    pin = torch.from_numpy(Pm).pin_memory()
+    cent = np.empty((N, 3))
+    n = max(1, args.steps)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        qhp.lib().qhp_set_modes(h, None, qhp.C.cast(pin.data_ptr(), qhp._DP))
+        step(h, 1)
+        qhp.lib().qhp_get_centroid(h, cent.ctypes.data_as(qhp._DP))
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    return {"value": N * P * n * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(Pm.nbytes),
+            "d2h_bytes_per_step": int(cent.nbytes)}
+
+
+def _fp64_path(args, cfg, dev):
+    """The same workload on the plain FP64 GPU path (FP64 pair math, FP64 forces)."""
+    import torch
+    from paper_2212_03137_b300 import qhp
+    s = qhp.System.from_config(cfg, precision="fp64")
+    stream = torch.cuda.current_stream(dev)
+    assert stream.cuda_stream != 0, "timing needs an explicit stream"
+    qhp.qhp_set_stream(s.h, stream.cuda_stream)
+    step = qhp.qhp_step_adqtb if cfg.thermostat == "adqtb" else qhp.qhp_step_rpmd
+    step(s.h, 1)
+    qhp.qhp_sync(s.h)
+    k = max(2, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(k):
+        e0.record(stream)
+        step(s.h, 1)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    s.close()
+    return {"value": s.n_atoms * s.P * k / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / k, "steps": k}
+
+
+def _oracle_sample(cfg, n_beads):
+    """Time the FP64 oracle (as it stands) on a bounded sample of one step: the forces of
+    n_beads of the P beads (oracle cell-list pair sum) plus one full BAOAB update of every mode.
+    Returns (seconds, atom-bead units covered, sampled bead positions, their oracle forces)."""
+    import math as _m
+    from oracle import rpmd as orp
+    from oracle import water as ow
+    from paper_2212_03137_b300.workloads import WATER_FF as W
+    box = cfg.system()
+    ff = ow.ForceField(eps=W["eps"], sigma=W["sigma"], q_O=W["q_O"], k_b=W["k_b"], r0=W["r0"],
+                       k_theta=W["k_theta"], theta0=_m.radians(W["theta0_deg"]), alpha=W["alpha"], rc=cfg.rc,
+                       m_O=W["m_O"], m_H=W["m_H"])
+    prm = orp.Params(P=cfg.P, temperature=cfg.temperature, dt=cfg.dt_fs * 1e-3, gamma0=cfg.gamma0, seed=cfg.seed)
+    m = ff.masses(box.types)
+    st = orp.init_state(box.pos, m, prm)
+    fn = ow.make_force_fn(box.types, box.molecule, box.box, ff, cells=True)
+    xb = orp.beads(st, cfg.P)[:n_beads]
+    t0 = time.perf_counter()
+    _, F = fn(xb)
+    t_force = time.perf_counter() - t0
+    st.f = np.zeros_like(st.Q)
+    t0 = time.perf_counter()
+    orp.kick(st, 0.5 * prm.dt)
+    orp.free_flow(st, prm, m, 0.5 * prm.dt)
+    orp.ou(st, prm, m, prm.dt)
+    orp.free_flow(st, prm, m, 0.5 * prm.dt)
+    orp.kick(st, 0.5 * prm.dt)
+    t_int = time.perf_counter() - t0
+    return t_force + t_int * n_beads / cfg.P, box.n_atoms * n_beads, xb, F, t_force, t_int
+
+
+def _cpu_baseline(cfg, args, n_beads=2):
+    """cpu_baseline leg: the oracle timed on the host cores, and the GPU force error on the
+    same sampled beads at the same initial state."""
+    from paper_2212_03137_b300 import qhp
+    t, units, xb, F, t_force, t_int = _oracle_sample(cfg, n_beads)
+    err = None
+    s = qhp.System.from_config(cfg)
+    try:
+        qhp.qhp_compute_forces(s.h)
+        Fg = qhp.qhp_get_forces(s.h)[:n_beads]
+        xg = qhp.qhp_get_beads(s.h)[:n_beads]
+        if np.abs(xg - xb).max() < 1e-9:
+            err = float(np.sqrt(np.sum((Fg - F) ** 2) / np.sum(F ** 2)))
+    finally:
+        s.close()
+    return ({"value": units / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"FP64 oracle: forces of {n_beads} of {cfg.P} beads ({t_force:.1f} s) + one BAOAB update "
+                       f"of all modes ({t_int:.2f} s) scaled by {n_beads}/{cfg.P}; numpy, 1 thread"}, err)
+
+
+def run_reference(args, ws, rank, local):
+    """Reference arm: the FP64 CPU oracle; each timed step is a one-bead sample of the workload."""
+    if rank != 0:
+        return None
+    cfg = _config(args.workload)
+    k = max(1, args.steps)
+    t_tot, units = 0.0, 0
+    for _ in range(k):
+        t, u, *_ = _oracle_sample(cfg, 1)
+        t_tot += t
+        units += u
+    value = units / t_tot
+    sample = f"FP64 oracle: forces of 1 of {cfg.P} beads + one BAOAB update of all modes scaled by 1/{cfg.P}"
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": k, "warmup": args.warmup,
+            "ms_per_step": t_tot / k * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "n_atoms": 3 * cfg.n_mol, "beads": cfg.P,
+                       "l2": "n/a (host CPU)", "parallelism": "single process"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def _profile_traffic(kind, workload):
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it is current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as fh:
+                d = json.load(fh)
+            v = d.get(workload, {}).get(kind)
+            return None if v is None else float(v)
+        except (OSError, ValueError):
+            return None
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rpmd_mixed_4096w")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-fp64", dest="fp64", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch
+        import torch.distributed as td
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        td.init_process_group(backend=backend)
+    out = run_ours(args, ws, rank, local) if args.impl == "ours" else run_reference(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * qhp.h - C ABI of the B300 (sm_103a) RPMD / adQTB time-step library.
+ *
+ * Method: Plé et al., "Routine molecular dynamics simulations including nuclear
+ * quantum effects: from force fields to machine learning potentials",
+ * arXiv 2212.03137.  Equation numbers follow the order of the paper's numbered
+ * display equations (Eq. (1) is the partition function of Sec. II.A).
+ *
+ * Conventions for every entry point
+ *   - units: kcal/mol, Angstrom, amu, ps (time steps are given in fs), e, K;
+ *   - arrays are C-contiguous; "[n][3]" means n rows of (x, y, z);
+ *   - host pointers are read or written synchronously and remain owned by the
+ *     caller; "_device" variants take device pointers (e.g. a torch tensor's
+ *     data_ptr()) that the library never frees, and work on the system's stream;
+ *   - the library owns all device memory of a system and frees it in
+ *     qhp_destroy_system;
+ *   - every call returns 0 (QHP_OK) or a negative QHP_ERR_* code; the message
+ *     of the last failure on the calling thread is qhp_last_error();
+ *   - step calls are asynchronous on the system's stream; a fault found on the
+ *     device (non-finite state, neighbour-list overflow) is reported by the next
+ *     call that synchronises (qhp_sync, the qhp_get_* calls) or by the next step
+ *     call.
+ */
+#ifndef QHP_H
+#define QHP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qhp_system_s* qhp_sys;
+
+enum {
+    QHP_OK = 0,
+    QHP_ERR_ARG = -1,           /* invalid argument or unsupported size */
+    QHP_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    QHP_ERR_TIMEOUT = -3,       /* a bounded device wait ran out */
+    QHP_ERR_NONFINITE = -4,     /* NaN/Inf found in the state */
+    QHP_ERR_LIST_OVERFLOW = -5, /* neighbour list larger than its buffer */
+    QHP_ERR_STATE = -6,         /* call out of order (e.g. step before set_beads) */
+    QHP_ERR_NOMEM = -7          /* device allocation failed */
+};
+
+enum { QHP_FP64 = 0, QHP_MIXED = 1 };
+enum { QHP_THERMO_PILE = 0, QHP_THERMO_ADQTB = 1, QHP_THERMO_NVE = 2 };
+enum { QHP_ADAPT_NONE = 0, QHP_ADAPT_SIMPLE = 1, QHP_ADAPT_RATIO = 2 };
+
+/* Interatomic potential V (the paper is independent of V; this is a flexible
+ * q-SPC/Fw-style water): O-O Lennard-Jones shifted to 0 at rc, damped-shifted-
+ * force Coulomb (damping alpha, 1/A) on all pairs of different molecules,
+ * 1/2 k_b (r - r0)^2 per O-H bond and 1/2 k_theta (theta - theta0)^2 per angle.
+ * q_H = -q_O / 2.  skin is the Verlet-list buffer (r_list = rc + skin). */
+typedef struct {
+    double eps, sigma, q_O;
+    double k_b, r0, k_theta, theta0; /* theta0 in radians */
+    double alpha, rc, skin;
+    double m_O, m_H;
+} qhp_ff;
+
+/* Thermostat.  PILE (Sec. III.A.1, Eq. (16)): friction gamma0 on the centroid
+ * and max(gamma0, omega_n) on mode n > 0.  ADQTB (Sec. II.B, Sec. III.B): single
+ * bead, colored noise of power Theta(omega) gamma(omega)/gamma0 per segment of
+ * n_seg steps, cut at omega_cut (cm^-1; <= 0 means no cut), gamma(omega)
+ * adapted per atom type at every segment end (adapt = QHP_ADAPT_*, rate
+ * a_gamma in ps^-1 per kcal/mol, RATIO time tau_ratio_ps) and clamped at
+ * gamma_min_frac * gamma0.  NVE: no friction and no noise on any mode (the
+ * ring-polymer equations of motion, Eq. (9), integrated as B A A B). */
+typedef struct {
+    int kind;
+    double gamma0;        /* ps^-1 */
+    double dt_fs;
+    int n_seg;
+    double omega_cut_cm;
+    double a_gamma;
+    double gamma_min_frac;
+    int adapt;
+    double tau_ratio_ps;
+} qhp_thermo;
+
+/* Estimators at the current state (kcal/mol).
+ * potential  = U_P = (1/P) sum_i V(x_i)                       (Eq. (3))
+ * spring     = sum_{n>0} 1/2 m omega_n^2 Q_n^2                 (Eq. (1))
+ * kinetic_nm = sum_n P_n^2 / 2m                               (Eq. (7))
+ * kinetic_cv = 3N kT/2 - (1/2P) sum_i (x_i - Q_0).F(x_i)      (Eq. (6))
+ * fdt_delta  = mean |Delta_bar_FDT| of the last segment, adQTB (Eq. (21)) */
+typedef struct {
+    double potential, spring, kinetic_nm, kinetic_cv, fdt_delta;
+    double bonded, nonbonded, reserved;
+} qhp_energy;
+
+typedef struct {
+    int n_atoms, P, precision, list_mode; /* list_mode 1: centroid Verlet list, 0: all pairs */
+    int64_t step, rebuilds, list_entries, list_capacity;
+    int64_t kernel_launches;              /* kernels this system has launched so far */
+    int n_cells_per_edge, reserved;
+} qhp_info;
+
+/* Create a system of n_atoms atoms in a cubic periodic box of edge box_L (A).
+ * type[i]: 0 = O, 1 = H.  Molecules are consecutive (O, H, H) triples with
+ * molecule[i] = i / 3.  pos: [n_atoms][3] initial positions (A), used as the
+ * centroids Q_0.  precision: QHP_FP64 or QHP_MIXED.  Allocates nothing on the
+ * device until qhp_set_beads.  Returns QHP_ERR_ARG for other layouts. */
+int qhp_create_system(qhp_sys* out, int n_atoms, const int* type, const int* molecule,
+                      const double* pos, double box_L, int precision);
+int qhp_destroy_system(qhp_sys sys);
+
+/* Set the potential (copied).  Must precede qhp_set_beads.  rc must be below box_L/2. */
+int qhp_set_forcefield(qhp_sys sys, const qhp_ff* ff);
+
+/* Allocate the P-bead state and initialise it (Eqs. (4), (7)): Q_0 = input
+ * positions, Q_n ~ N(0, kT/(m omega_n^2)) for n > 0, P_n ~ N(0, m kT), drawn
+ * from Philox4x32-10 with key = seed.  P must be a power of two, 1 <= P <= 64.
+ * Resets the step counter. */
+int qhp_set_beads(qhp_sys sys, int P, double temperature_K, uint64_t seed);
+
+/* Set the thermostat and time step (copied).  For ADQTB, P must be 1 and
+ * n_seg a power of two in [4, 2048]; the first noise segment is generated here. */
+int qhp_set_thermostat(qhp_sys sys, const qhp_thermo* th);
+
+/* Advance n BAOAB steps (Eq. (17)) with the PILE thermostat, or with the adQTB
+ * O step for qhp_step_adqtb.  Asynchronous; n >= 0. */
+int qhp_step_rpmd(qhp_sys sys, int n);
+int qhp_step_adqtb(qhp_sys sys, int n);
+
+/* Evaluate bead forces at the current modes (no time step). */
+int qhp_compute_forces(qhp_sys sys);
+
+/* Synchronise the stream and report device-side faults. */
+int qhp_sync(qhp_sys sys);
+
+int qhp_get_energy(qhp_sys sys, qhp_energy* out);
+/* Bead forces -grad V(x_i) of the last force evaluation, out[P][n_atoms][3]. */
+int qhp_get_forces(qhp_sys sys, double* out);
+/* Centroids Q_0, out[n_atoms][3] (unwrapped). */
+int qhp_get_centroid(qhp_sys sys, double* out);
+/* Bead positions x_i = sqrt(P) sum_n T_in Q_n in FP64 (Eq. (4)), out[P][n_atoms][3]. */
+int qhp_get_beads(qhp_sys sys, double* out);
+/* Normal-mode state, Q[n_atoms][3][P] (A) and Pm[n_atoms][3][P] (amu A/ps). */
+int qhp_get_modes(qhp_sys sys, double* Q, double* Pm);
+/* Replace the mode state (copied); the next step re-evaluates forces and the list. */
+int qhp_set_modes(qhp_sys sys, const double* Q, const double* Pm);
+/* Device-pointer variants: same layouts, on the system's stream. */
+int qhp_set_modes_device(qhp_sys sys, const double* Q, const double* Pm);
+int qhp_get_modes_device(qhp_sys sys, double* Q, double* Pm);
+int qhp_get_forces_device(qhp_sys sys, double* out);
+
+/* Checkpoint: opaque blob of the whole dynamical state (modes, forces, step,
+ * adQTB gamma, noise segment and records).  qhp_get_state with buf == NULL
+ * writes the required size to *size. */
+int qhp_get_state(qhp_sys sys, void* buf, size_t* size);
+int qhp_set_state(qhp_sys sys, const void* buf, size_t size);
+
+/* adQTB: gamma_z(omega_j), out[2][n_seg + 1] (type 0 = O, 1 = H), ps^-1. */
+int qhp_get_gamma(qhp_sys sys, double* out);
+int qhp_set_gamma(qhp_sys sys, const double* in);
+/* adQTB: current colored-noise segment u[n_seg][3 n_atoms] (sqrt(kcal/mol)) and
+ * the records of the current segment v[n_seg][3n] (A/ps), F[n_seg][3n] (amu A/ps^2). */
+int qhp_get_qtb_noise(qhp_sys sys, float* u);
+int qhp_get_qtb_records(qhp_sys sys, float* v, float* F);
+
+/* Centroid neighbour structures (Sec. III.A.3), for inspection and tests.
+ * qhp_build_list rebuilds them from the current centroids.
+ * qhp_get_cells: cell id of each atom [n_atoms] and the sorted order
+ * (position -> atom) [n_atoms].  qhp_get_list_pairs: the unordered pairs
+ * (i < j, atom indices) of the list, at most cap of them; *count receives the
+ * total. */
+int qhp_build_list(qhp_sys sys);
+int qhp_get_cells(qhp_sys sys, int* cell, int* order);
+int qhp_get_list_pairs(qhp_sys sys, int64_t* pairs, int64_t cap, int64_t* count);
+
+int qhp_get_info(qhp_sys sys, qhp_info* out);
+
+/* Measurement hooks.  With profiling on, every step records CUDA events on the
+ * system's stream around its stages (they are captured into the step graph);
+ * qhp_get_profile synchronises and returns the stage durations of the last step
+ * (ms): B-A-O-A + bead positions, list check/rebuild, nonbonded pair kernel,
+ * bonded kernel, force projection + B, and the whole step. */
+typedef struct {
+    float integrate_ms, list_ms, pair_ms, bonded_ms, project_ms, step_ms;
+} qhp_profile;
+int qhp_set_profiling(qhp_sys sys, int on);
+int qhp_get_profile(qhp_sys sys, qhp_profile* out);
+/* Number of bead pairs (each unordered pair once, summed over beads) within rc
+ * at the current positions, and how many of them are O-O (LJ) pairs. */
+int qhp_count_pairs(qhp_sys sys, int64_t* pairs, int64_t* oo_pairs);
+/* Use an external CUDA stream (cudaStream_t passed as void*); NULL restores the
+ * library's own stream. */
+int qhp_set_stream(qhp_sys sys, void* stream);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* qhp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

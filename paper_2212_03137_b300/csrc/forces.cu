@@ -1,0 +1,498 @@
+// Bead-batched forces: nonbonded pairs from the centroid list and bonded terms.
+//
+// Pair kernel mapping: one warp per sorted atom i.  The centroid list is shared
+// by all beads (Sec. III.A.3), so the lanes of a warp take the *beads* of i:
+// for P >= 32 every lane owns P/32 beads and all lanes walk the same list entry
+// (no divergence, one coalesced 128-byte load per coordinate plane); for P < 32
+// the warp takes 32/P list entries at a time, lane = (entry slot, bead).  The
+// full list is walked (each pair twice), so forces on i accumulate in registers
+// and are written once: no atomics, and the result does not depend on timing.
+//
+// Mixed precision: positions are FP32 offsets from the atom's anchor (its
+// centroid at the last list build), each list entry carries the FP32 anchor
+// separation D_ij (rounded once from FP64), so d = D_ij + (x_j - x_i) stays
+// accurate to ~5e-7 A in boxes of any size.  Pair math is FP32; the per-lane
+// sum is converted once to int64 fixed point (2^-34 kcal/mol/A), to which the
+// bonded kernel adds its own integer contribution, so bead sums are exact.
+//
+// FP64 path: absolute FP64 positions, minimum image per pair, FP64 math and
+// FP64 forces.
+#include <math.h>
+
+#include "qhp_internal.cuh"
+
+namespace qhp {
+
+namespace {
+
+struct PairConsts {
+    float rc2, rc, alpha, c2a, sc, ecut, sig2, eps4, eps24, ljshift, L, invL;
+    double rc2_d, rc_d, alpha_d, c2a_d, sc_d, ecut_d, sig2_d, eps4_d, eps24_d, ljshift_d, L_d, invL_d, ke_d;
+    float ke, qO_ke, qH_ke;
+};
+
+// List entries carry the partner's sorted index in the low 31 bits and "partner is H"
+// in bit 31, so the partner's charge and LJ flag need no extra load.
+constexpr int ENTRY_H_BIT = (int)0x80000000u;
+__device__ __forceinline__ int entry_j(int x) { return x & 0x7fffffff; }
+__device__ __forceinline__ bool entry_is_h(int x) { return x < 0; }
+
+// erfc(x) for x >= 0 with fractional error below 1.2e-7 everywhere: the Chebyshev fit
+// published in Numerical Recipes in C (2nd ed., Sec. 6.2, function erfcc),
+// erfc(x) = t exp(-x^2 + poly(t)), t = 1/(1 + x/2).  gauss receives exp(-x^2).
+__device__ __forceinline__ float erfc_cheb(float x, float& gauss) {
+    const float t = __fdividef(1.0f, fmaf(0.5f, x, 1.0f));
+    float p = 0.17087277f;
+    p = fmaf(p, t, -0.82215223f);
+    p = fmaf(p, t, 1.48851587f);
+    p = fmaf(p, t, -1.13520398f);
+    p = fmaf(p, t, 0.27886807f);
+    p = fmaf(p, t, -0.18628806f);
+    p = fmaf(p, t, 0.09678418f);
+    p = fmaf(p, t, 0.37409196f);
+    p = fmaf(p, t, 1.00002368f);
+    p = fmaf(p, t, -1.26551223f);
+    gauss = __expf(-x * x);
+    return t * gauss * __expf(p);
+}
+
+// One bead pair: DSF Coulomb (+ shifted LJ on O-O), force on i accumulated as -g d.
+template <bool ALL, bool ENERGY>
+__device__ __forceinline__ void pair_term(float dx, float dy, float dz, float qq, bool lj, const PairConsts& c,
+                                          float& fx, float& fy, float& fz, float& en) {
+    if (ALL) {
+        dx -= c.L * rintf(dx * c.invL);
+        dy -= c.L * rintf(dy * c.invL);
+        dz -= c.L * rintf(dz * c.invL);
+    }
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 < c.rc2) {
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        float gauss;
+        const float erfc_ar = erfc_cheb(c.alpha * r, gauss);
+        const float rinv2 = rinv * rinv;
+        // -V'(r)/r = qq (erfc(a r)/r^2 + (2a/sqrt(pi)) e^{-a^2 r^2}/r - S_c) / r
+        float g = qq * fmaf(erfc_ar, rinv2, fmaf(c.c2a * gauss, rinv, -c.sc)) * rinv;
+        float ep = 0.0f;
+        if (ENERGY) ep = qq * (erfc_ar * rinv - c.ecut + c.sc * (r - c.rc));
+        if (lj) {
+            const float s2 = c.sig2 * rinv2;
+            const float s6 = s2 * s2 * s2;
+            g = fmaf(c.eps24 * fmaf(2.0f * s6, s6, -s6), rinv2, g);
+            if (ENERGY) ep += c.eps4 * (s6 * s6 - s6) - c.ljshift;
+        }
+        fx = fmaf(-g, dx, fx);
+        fy = fmaf(-g, dy, fy);
+        fz = fmaf(-g, dz, fz);
+        if (ENERGY) en = fmaf(0.5f, ep, en);
+    }
+}
+
+template <int P, bool ALL, bool ENERGY>
+__global__ void __launch_bounds__(128) k_pair_mixed(int N, const float* __restrict__ pos, const int* __restrict__ start,
+                                                    const int4* __restrict__ nbr, const float* __restrict__ charge_s,
+                                                    const int* __restrict__ type_s, const int* __restrict__ perm,
+                                                    long long* __restrict__ F, float* __restrict__ epair, PairConsts c,
+                                                    const unsigned* __restrict__ status) {
+    constexpr int JPW = P >= 32 ? 1 : 32 / P;
+    constexpr int BPL = P > 32 ? P / 32 : 1;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    const int b0 = P >= 32 ? lane : (lane % P);
+    const int jsub = P >= 32 ? 0 : lane / P;
+    const bool ok = (*status & ST_LIST_OVERFLOW) == 0u;
+    const float* __restrict__ px = pos;
+    const float* __restrict__ py = pos + (size_t)N * P;
+    const float* __restrict__ pz = pos + (size_t)2 * N * P;
+
+    float xi[BPL], yi[BPL], zi[BPL], fx[BPL], fy[BPL], fz[BPL], en[BPL];
+#pragma unroll
+    for (int u = 0; u < BPL; ++u) {
+        const size_t o = (size_t)i * P + b0 + 32 * u;
+        xi[u] = px[o];
+        yi[u] = py[o];
+        zi[u] = pz[o];
+        fx[u] = fy[u] = fz[u] = en[u] = 0.0f;
+    }
+    const float qi = charge_s[i];
+    const bool Oi = type_s[i] == 0;
+    const float qO = qi * c.qO_ke, qH = qi * c.qH_ke;
+    const int k1 = ok ? start[i + 1] : start[i];
+    int k = start[i] + jsub;
+    // two list entries per iteration: both entries and all their loads are in flight together
+    for (; k + JPW < k1; k += 2 * JPW) {
+        const int4 e0 = __ldg(&nbr[k]);
+        const int4 e1 = __ldg(&nbr[k + JPW]);
+        const int j0 = entry_j(e0.x), j1 = entry_j(e1.x);
+        const bool h0 = entry_is_h(e0.x), h1 = entry_is_h(e1.x);
+#pragma unroll
+        for (int u = 0; u < BPL; ++u) {
+            const size_t o0 = (size_t)j0 * P + b0 + 32 * u, o1 = (size_t)j1 * P + b0 + 32 * u;
+            const float ax = __ldg(&px[o0]), ay = __ldg(&py[o0]), az = __ldg(&pz[o0]);
+            const float bx = __ldg(&px[o1]), by = __ldg(&py[o1]), bz = __ldg(&pz[o1]);
+            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (ax - xi[u]), __int_as_float(e0.z) + (ay - yi[u]),
+                                   __int_as_float(e0.w) + (az - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u], fy[u],
+                                   fz[u], en[u]);
+            pair_term<ALL, ENERGY>(__int_as_float(e1.y) + (bx - xi[u]), __int_as_float(e1.z) + (by - yi[u]),
+                                   __int_as_float(e1.w) + (bz - zi[u]), h1 ? qH : qO, Oi && !h1, c, fx[u], fy[u],
+                                   fz[u], en[u]);
+        }
+    }
+    if (k < k1) {
+        const int4 e0 = __ldg(&nbr[k]);
+        const int j0 = entry_j(e0.x);
+        const bool h0 = entry_is_h(e0.x);
+#pragma unroll
+        for (int u = 0; u < BPL; ++u) {
+            const size_t o0 = (size_t)j0 * P + b0 + 32 * u;
+            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (__ldg(&px[o0]) - xi[u]),
+                                   __int_as_float(e0.z) + (__ldg(&py[o0]) - yi[u]),
+                                   __int_as_float(e0.w) + (__ldg(&pz[o0]) - zi[u]), h0 ? qH : qO, Oi && !h0, c,
+                                   fx[u], fy[u], fz[u], en[u]);
+        }
+    }
+    if (P < 32) {
+#pragma unroll
+        for (int off = (P < 32 ? P : 16); off < 32; off <<= 1) {
+            fx[0] += __shfl_xor_sync(0xffffffffu, fx[0], off);
+            fy[0] += __shfl_xor_sync(0xffffffffu, fy[0], off);
+            fz[0] += __shfl_xor_sync(0xffffffffu, fz[0], off);
+            if (ENERGY) en[0] += __shfl_xor_sync(0xffffffffu, en[0], off);
+        }
+    }
+    if (jsub == 0) {
+        const int a = perm[i];
+#pragma unroll
+        for (int u = 0; u < BPL; ++u) {
+            const int b = b0 + 32 * u;
+            F[((size_t)a * 3 + 0) * P + b] = __float2ll_rn(fx[u] * FIX_SCALE_F);
+            F[((size_t)a * 3 + 1) * P + b] = __float2ll_rn(fy[u] * FIX_SCALE_F);
+            F[((size_t)a * 3 + 2) * P + b] = __float2ll_rn(fz[u] * FIX_SCALE_F);
+            if (ENERGY) epair[(size_t)i * P + b] = en[u];
+        }
+    }
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(128) k_pair_fp64(int N, int P, const double* __restrict__ pos,
+                                                   const int* __restrict__ start, const int4* __restrict__ nbr,
+                                                   const float* __restrict__ charge_s, const int* __restrict__ type_s,
+                                                   const int* __restrict__ perm, const double q_O, const double q_H,
+                                                   double* __restrict__ F, double* __restrict__ epair, PairConsts c,
+                                                   const unsigned* __restrict__ status) {
+    // lane = (entry slot, bead) as in the mixed kernel, with P <= 32 handled by slots and
+    // P = 64 by two beads per lane.
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    const int JPW = P >= 32 ? 1 : 32 / P;
+    const int BPL = P > 32 ? P / 32 : 1;
+    const int b0 = P >= 32 ? lane : (lane % P);
+    const int jsub = P >= 32 ? 0 : lane / P;
+    const bool ok = (*status & ST_LIST_OVERFLOW) == 0u;
+    const double qi = (type_s[i] == 0 ? q_O : q_H) * c.ke_d;
+    const bool Oi = type_s[i] == 0;
+    const int k0 = start[i], k1 = ok ? start[i + 1] : start[i];
+    for (int u = 0; u < BPL; ++u) {
+        const int b = b0 + 32 * u;
+        const double xi = pos[((size_t)0 * N + i) * P + b];
+        const double yi = pos[((size_t)1 * N + i) * P + b];
+        const double zi = pos[((size_t)2 * N + i) * P + b];
+        double fx = 0.0, fy = 0.0, fz = 0.0, en = 0.0;
+        for (int k = k0 + jsub; k < k1; k += JPW) {
+            const int ex = __ldg(&nbr[k].x);
+            const int j = entry_j(ex);
+            const bool Oj = !entry_is_h(ex);
+            const double qq = qi * (Oj ? q_O : q_H);
+            double dx = pos[((size_t)0 * N + j) * P + b] - xi;
+            double dy = pos[((size_t)1 * N + j) * P + b] - yi;
+            double dz = pos[((size_t)2 * N + j) * P + b] - zi;
+            dx -= c.L_d * rint(dx * c.invL_d);
+            dy -= c.L_d * rint(dy * c.invL_d);
+            dz -= c.L_d * rint(dz * c.invL_d);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < c.rc2_d) {
+                const double r = sqrt(r2);
+                const double rinv = 1.0 / r;
+                const double ar = c.alpha_d * r;
+                const double erfc_ar = erfc(ar);
+                const double ex = exp(-ar * ar);
+                const double rinv2 = rinv * rinv;
+                double g = qq * (erfc_ar * rinv2 + c.c2a_d * ex * rinv - c.sc_d) * rinv;
+                double ep = 0.0;
+                if (ENERGY) ep = qq * (erfc_ar * rinv - c.ecut_d + c.sc_d * (r - c.rc_d));
+                if (Oi && Oj) {
+                    const double s2 = c.sig2_d * rinv2;
+                    const double s6 = s2 * s2 * s2;
+                    g += c.eps24_d * (2.0 * s6 * s6 - s6) * rinv2;
+                    if (ENERGY) ep += c.eps4_d * (s6 * s6 - s6) - c.ljshift_d;
+                }
+                fx -= g * dx;
+                fy -= g * dy;
+                fz -= g * dz;
+                if (ENERGY) en += 0.5 * ep;
+            }
+        }
+        for (int off = (P < 32 ? P : 32); off < 32; off <<= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, off);
+            fy += __shfl_xor_sync(0xffffffffu, fy, off);
+            fz += __shfl_xor_sync(0xffffffffu, fz, off);
+            if (ENERGY) en += __shfl_xor_sync(0xffffffffu, en, off);
+        }
+        if (jsub == 0) {
+            const int a = perm[i];
+            F[((size_t)a * 3 + 0) * P + b] = fx;
+            F[((size_t)a * 3 + 1) * P + b] = fy;
+            F[((size_t)a * 3 + 2) * P + b] = fz;
+            if (ENERGY) epair[(size_t)i * P + b] = en;
+        }
+    }
+}
+
+struct BondConsts {
+    double kb, r0, kth, th0, L;
+};
+
+// Bonded terms per (molecule, bead); each thread owns the forces of its three atoms at its bead.
+template <bool MIXED, bool ENERGY>
+__global__ void k_bonded(int n_mol, int N, int P, const float* __restrict__ pos_f, const double* __restrict__ pos_d,
+                         const float* __restrict__ dA, const int* __restrict__ iperm, long long* Ffix, double* Fd,
+                         double* ebond, BondConsts c) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_mol * P) return;
+    const int m = t / P, b = t % P;
+    const int aO = 3 * m, aH1 = aO + 1, aH2 = aO + 2;
+    const int sO = iperm[aO], s1 = iperm[aH1], s2 = iperm[aH2];
+    if (MIXED) {
+        float d1[3], d2[3];
+        for (int d = 0; d < 3; ++d) {
+            const float xo = pos_f[((size_t)d * N + sO) * P + b];
+            d1[d] = (pos_f[((size_t)d * N + s1) * P + b] - xo) + dA[((size_t)m * 2 + 0) * 4 + d];
+            d2[d] = (pos_f[((size_t)d * N + s2) * P + b] - xo) + dA[((size_t)m * 2 + 1) * 4 + d];
+        }
+        const float r1 = sqrtf(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+        const float r2 = sqrtf(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+        float cs = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
+        cs = fminf(1.0f, fmaxf(-1.0f, cs));
+        const float th = acosf(cs);
+        const float sn = sqrtf(fmaxf(1e-30f, 1.0f - cs * cs));
+        const float kb = (float)c.kb, r0 = (float)c.r0, kth = (float)c.kth, th0 = (float)c.th0;
+        const float pb1 = -kb * (r1 - r0) / r1, pb2 = -kb * (r2 - r0) / r2;
+        const float pa = kth * (th - th0) / sn;
+        const float ir12 = 1.0f / (r1 * r2);
+        for (int d = 0; d < 3; ++d) {
+            const float f1 = pb1 * d1[d] + pa * (d2[d] * ir12 - cs * d1[d] / (r1 * r1));
+            const float f2 = pb2 * d2[d] + pa * (d1[d] * ir12 - cs * d2[d] / (r2 * r2));
+            const long long i1 = __float2ll_rn(f1 * FIX_SCALE_F), i2 = __float2ll_rn(f2 * FIX_SCALE_F);
+            Ffix[((size_t)aH1 * 3 + d) * P + b] += i1;
+            Ffix[((size_t)aH2 * 3 + d) * P + b] += i2;
+            Ffix[((size_t)aO * 3 + d) * P + b] -= i1 + i2;
+        }
+        if (ENERGY)
+            ebond[t] = 0.5 * c.kb * ((double)(r1 - r0) * (r1 - r0) + (double)(r2 - r0) * (r2 - r0)) +
+                       0.5 * c.kth * (double)(th - th0) * (th - th0);
+    } else {
+        double d1[3], d2[3];
+        for (int d = 0; d < 3; ++d) {
+            const double xo = pos_d[((size_t)d * N + sO) * P + b];
+            double a1 = pos_d[((size_t)d * N + s1) * P + b] - xo;
+            double a2 = pos_d[((size_t)d * N + s2) * P + b] - xo;
+            d1[d] = a1 - c.L * rint(a1 / c.L);
+            d2[d] = a2 - c.L * rint(a2 / c.L);
+        }
+        const double r1 = sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+        const double r2 = sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+        double cs = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
+        cs = fmin(1.0, fmax(-1.0, cs));
+        const double th = acos(cs);
+        const double sn = sqrt(fmax(1e-300, 1.0 - cs * cs));
+        const double pb1 = -c.kb * (r1 - c.r0) / r1, pb2 = -c.kb * (r2 - c.r0) / r2;
+        const double pa = c.kth * (th - c.th0) / sn;
+        const double ir12 = 1.0 / (r1 * r2);
+        for (int d = 0; d < 3; ++d) {
+            const double f1 = pb1 * d1[d] + pa * (d2[d] * ir12 - cs * d1[d] / (r1 * r1));
+            const double f2 = pb2 * d2[d] + pa * (d1[d] * ir12 - cs * d2[d] / (r2 * r2));
+            Fd[((size_t)aH1 * 3 + d) * P + b] += f1;
+            Fd[((size_t)aH2 * 3 + d) * P + b] += f2;
+            Fd[((size_t)aO * 3 + d) * P + b] -= f1 + f2;
+        }
+        if (ENERGY)
+            ebond[t] = 0.5 * c.kb * ((r1 - c.r0) * (r1 - c.r0) + (r2 - c.r0) * (r2 - c.r0)) +
+                       0.5 * c.kth * (th - c.th0) * (th - c.th0);
+    }
+}
+
+// Count in-cutoff bead pairs j > i (lane = bead, one list entry at a time); not on the step path.
+__global__ void k_count_pairs(int N, int P, int mixed, int all, const float* __restrict__ pos_f,
+                              const double* __restrict__ pos_d, const int* __restrict__ start,
+                              const int4* __restrict__ nbr, const int* __restrict__ type_s, PairConsts c,
+                              unsigned long long* out2) {
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    unsigned long long n = 0, noo = 0;
+    for (int b = lane; b < P; b += 32) {
+        for (int k = start[i]; k < start[i + 1]; ++k) {
+            const int4 e = nbr[k];
+            const int j = entry_j(e.x);
+            if (j <= i) continue;
+            double r2;
+            if (mixed) {
+                float dx = __int_as_float(e.y) + (pos_f[((size_t)0 * N + j) * P + b] - pos_f[((size_t)0 * N + i) * P + b]);
+                float dy = __int_as_float(e.z) + (pos_f[((size_t)1 * N + j) * P + b] - pos_f[((size_t)1 * N + i) * P + b]);
+                float dz = __int_as_float(e.w) + (pos_f[((size_t)2 * N + j) * P + b] - pos_f[((size_t)2 * N + i) * P + b]);
+                if (all) {
+                    dx -= c.L * rintf(dx * c.invL);
+                    dy -= c.L * rintf(dy * c.invL);
+                    dz -= c.L * rintf(dz * c.invL);
+                }
+                r2 = (double)(dx * dx + dy * dy + dz * dz);
+                if (!((float)r2 < c.rc2)) continue;
+            } else {
+                double d[3];
+                for (int q = 0; q < 3; ++q) {
+                    d[q] = pos_d[((size_t)q * N + j) * P + b] - pos_d[((size_t)q * N + i) * P + b];
+                    d[q] -= c.L_d * rint(d[q] * c.invL_d);
+                }
+                r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!(r2 < c.rc2_d)) continue;
+            }
+            ++n;
+            noo += (type_s[i] == 0 && type_s[j] == 0);
+        }
+    }
+    atomicAdd(&out2[0], n);
+    atomicAdd(&out2[1], noo);
+}
+
+PairConsts make_pair_consts(const qhp_system_s* s) {
+    const qhp_ff& f = s->ff;
+    PairConsts c;
+    const double rc = f.rc, a = f.alpha;
+    const double sc = erfc(a * rc) / (rc * rc) + 2.0 * a / sqrt(M_PI) * exp(-(a * rc) * (a * rc)) / rc;
+    const double ecut = erfc(a * rc) / rc;
+    const double sr6 = pow(f.sigma / rc, 6.0);
+    const double ljs = 4.0 * f.eps * (sr6 * sr6 - sr6);
+    c.rc2_d = rc * rc;
+    c.rc_d = rc;
+    c.alpha_d = a;
+    c.c2a_d = 2.0 * a / sqrt(M_PI);
+    c.sc_d = sc;
+    c.ecut_d = ecut;
+    c.sig2_d = f.sigma * f.sigma;
+    c.eps4_d = 4.0 * f.eps;
+    c.eps24_d = 24.0 * f.eps;
+    c.ljshift_d = ljs;
+    c.L_d = s->L;
+    c.invL_d = 1.0 / s->L;
+    c.ke_d = COULOMB;
+    c.rc2 = (float)c.rc2_d;
+    c.rc = (float)rc;
+    c.alpha = (float)a;
+    c.c2a = (float)c.c2a_d;
+    c.sc = (float)sc;
+    c.ecut = (float)ecut;
+    c.sig2 = (float)c.sig2_d;
+    c.eps4 = (float)c.eps4_d;
+    c.eps24 = (float)c.eps24_d;
+    c.ljshift = (float)ljs;
+    c.L = (float)s->L;
+    c.invL = (float)(1.0 / s->L);
+    c.ke = (float)COULOMB;
+    c.qO_ke = (float)(COULOMB * f.q_O);
+    c.qH_ke = (float)(COULOMB * (-0.5 * f.q_O));
+    return c;
+}
+
+template <int P>
+void pair_mixed_dispatch(qhp_system_s* s, bool energy, const PairConsts& c, int grid) {
+    if (s->list_mode) {
+        if (energy)
+            k_pair_mixed<P, false, true><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr, s->charge_s,
+                                                                      s->type_s, s->perm, s->Ffix, s->e_pair, c,
+                                                                      s->status);
+        else
+            k_pair_mixed<P, false, false><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr,
+                                                                       s->charge_s, s->type_s, s->perm, s->Ffix,
+                                                                       s->e_pair, c, s->status);
+    } else {
+        if (energy)
+            k_pair_mixed<P, true, true><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr, s->charge_s,
+                                                                     s->type_s, s->perm, s->Ffix, s->e_pair, c,
+                                                                     s->status);
+        else
+            k_pair_mixed<P, true, false><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr,
+                                                                      s->charge_s, s->type_s, s->perm, s->Ffix,
+                                                                      s->e_pair, c, s->status);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pair(qhp_system_s* s, bool energy) {
+    const PairConsts c = make_pair_consts(s);
+    const int grid = (s->N * 32 + 127) / 128;
+    if (s->precision == QHP_MIXED) {
+        switch (s->P) {
+            case 1: pair_mixed_dispatch<1>(s, energy, c, grid); break;
+            case 2: pair_mixed_dispatch<2>(s, energy, c, grid); break;
+            case 4: pair_mixed_dispatch<4>(s, energy, c, grid); break;
+            case 8: pair_mixed_dispatch<8>(s, energy, c, grid); break;
+            case 16: pair_mixed_dispatch<16>(s, energy, c, grid); break;
+            case 32: pair_mixed_dispatch<32>(s, energy, c, grid); break;
+            case 64: pair_mixed_dispatch<64>(s, energy, c, grid); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        if (energy)
+            k_pair_fp64<true><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr, s->charge_s,
+                                                           s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O, s->Fd,
+                                                           s->e_pair_d, c, s->status);
+        else
+            k_pair_fp64<false><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr, s->charge_s,
+                                                            s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O, s->Fd,
+                                                            s->e_pair_d, c, s->status);
+    }
+    s->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bonded(qhp_system_s* s, bool energy) {
+    BondConsts bc{s->ff.k_b, s->ff.r0, s->ff.k_theta, s->ff.theta0, s->L};
+    const int nt = s->n_mol * s->P;
+    const int g2 = (nt + 127) / 128;
+    const bool mixed = s->precision == QHP_MIXED;
+    if (mixed) {
+        if (energy) k_bonded<true, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+        else k_bonded<true, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+    } else {
+        if (energy) k_bonded<false, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+        else k_bonded<false, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+    }
+    s->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(qhp_system_s* s, bool energy) {
+    cudaError_t e = launch_pair(s, energy);
+    if (e != cudaSuccess) return e;
+    if (s->prof_on) {
+        e = cudaEventRecordWithFlags(s->prof_ev[3], s->stream, cudaEventRecordExternal);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_bonded(s, energy);
+}
+
+// In-cutoff bead pairs (each unordered pair once) and how many of them are O-O.
+cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2) {
+    const PairConsts c = make_pair_consts(s);
+    const int grid = (s->N * 32 + 127) / 128;
+    k_count_pairs<<<grid, 128, 0, s->stream>>>(s->N, s->P, s->precision == QHP_MIXED, s->list_mode, s->pos_f, s->pos_d,
+                                               s->nbr_start, s->nbr, s->type_s, c, out2);
+    s->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace qhp

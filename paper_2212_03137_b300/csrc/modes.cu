@@ -1,0 +1,474 @@
+// Normal-mode kernels: initial state, BAOAB propagation in modes, bead positions,
+// force projection and the estimators.
+//
+// Layout: modes Q, Pm, projected forces fmode and bead forces are [atom][dim][P]
+// (mode / bead index innermost, original atom order).  A block holds
+// APB = 64/P whole atoms, i.e. 3*P*APB = 192 threads, one per (atom, dim, mode),
+// so the P x P bead transform of an atom happens in shared memory.
+#include <math.h>
+
+#include "qhp_internal.cuh"
+
+namespace qhp {
+
+namespace {
+
+constexpr int BLOCK = 192;
+
+struct IntegrateArgs {
+    int N, P, apb, n_seg;
+    double half_dt_acc, inv_dt;
+    uint64_t seed;
+    const unsigned long long* step_ctr;
+    double *Q, *Pm;
+    const double* fmode;
+    const int* type;
+    const double* tab;     // per (atom type, mode): MT_* entries
+    const double* anchor;
+    const int* iperm;
+    const double* Tm;      // sqrt(P) T[b][n]
+    const float* Tmf;
+    float* pos_f;
+    double* pos_d;
+    unsigned* dev_max;
+    const float* qtb_u;
+    float *qtb_v, *qtb_F;
+    const int* gate;       // if set, the kernel runs only when *gate != 0
+};
+
+__device__ __forceinline__ void block_max_atomic(float v, unsigned* out) {
+    __shared__ float wmax[BLOCK / 32];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = wmax[0];
+        for (int w = 1; w < BLOCK / 32; ++w) m = fmaxf(m, wmax[w]);
+        atomicMax(out, __float_as_uint(m));   // m >= 0: float order == unsigned order
+    }
+}
+
+// Exact free flow over dt/2 (Eq. (9) without forces): drift for the centroid, the
+// three-shear form of the rotation for n > 0 (determinant one whatever the rounding).
+__device__ __forceinline__ void free_half(int n, const double* c, double& q, double& pm) {
+    if (n == 0) {
+        q += pm * c[MT_SA];
+    } else {
+        q += c[MT_SA] * pm;
+        pm -= c[MT_SB] * q;
+        q += c[MT_SA] * pm;
+    }
+}
+
+// B(dt/2) A(dt/2) O(dt) A(dt/2) on each mode (Eq. (17)), then x = sqrt(P) T Q (Eq. (4)).
+// INTEGRATE = false only recomputes bead positions (after a list rebuild or set_modes).
+template <bool MIXED, bool ADQTB, bool INTEGRATE>
+__global__ void __launch_bounds__(BLOCK) k_integrate(IntegrateArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    if (A.gate && !*A.gate) return;                                   // uniform over the grid
+    const int P = A.P;
+    double* qs = reinterpret_cast<double*>(smem_raw);                 // [BLOCK]
+    float* qf = reinterpret_cast<float*>(qs + BLOCK);                 // [BLOCK]
+    float* xr = qf + BLOCK;                                           // [BLOCK]
+    float* Tsf = reinterpret_cast<float*>(smem_raw + BLOCK * 16);      // [P*P] (mixed), mode-major
+    double* Tsd = reinterpret_cast<double*>(smem_raw + BLOCK * 16);    // [P*P] (fp64), mode-major
+
+    const int t = threadIdx.x;
+    const int la = t / (3 * P), d = (t / P) % 3, n = t % P;
+    const int a = blockIdx.x * A.apb + la;
+    const bool valid = a < A.N;
+    const int idx = (a * 3 + d) * P + n;
+
+    // transpose to [mode k][bead b] so that the lanes (beads) of a warp read consecutive words
+    for (int e = t; e < P * P; e += BLOCK) {
+        const int b = e / P, k = e % P;
+        if (MIXED) Tsf[k * P + b] = A.Tmf[e];
+        else Tsd[k * P + b] = A.Tm[e];
+    }
+
+    double q = 0.0, pm = 0.0;
+    if (valid) {
+        q = A.Q[idx];
+        pm = A.Pm[idx];
+        if (INTEGRATE) {
+            const double* c = A.tab + ((size_t)A.type[a] * P + n) * MT_N;
+            const unsigned long long step = *A.step_ctr;
+            pm += A.half_dt_acc * A.fmode[idx];                       // B
+            free_half(n, c, q, pm);                                   // A
+            if (ADQTB) {                                              // O with colored noise
+                const int dof = a * 3 + d;
+                const int ms = (int)(step % (unsigned long long)A.n_seg);
+                const size_t r = (size_t)ms * (size_t)(3 * A.N) + dof;
+                const double kick = c[MT_AMP] * (double)A.qtb_u[r];
+                const double pnew = c[MT_C1] * pm + kick;
+                A.qtb_v[r] = (float)((pm + pnew) * c[MT_INV2M]);
+                A.qtb_F[r] = (float)(kick * A.inv_dt);
+                pm = pnew;
+            } else {                                                  // O with white noise
+                const uint4 x = philox_draw(A.seed, (uint32_t)idx, step, TAG_OSTEP);
+                const double R = MIXED ? (double)normal_f32(x, 0) : normal_f64(x, 0);
+                pm = c[MT_C1] * pm + c[MT_AMP] * R;
+            }
+            free_half(n, c, q, pm);                                   // A
+            A.Q[idx] = q;
+            A.Pm[idx] = pm;
+        }
+    }
+    qs[t] = q;
+    qf[t] = (float)q;
+    __syncthreads();
+
+    float dv = 0.0f;
+    if (valid) {
+        const int base = la * 3 * P + d * P;
+        const int s = A.iperm[a];
+        const double anc = A.anchor[a * 3 + d];
+        if (MIXED) {
+            // FP64 centroid offset + FP32 fluctuation sum: the bead position only feeds the
+            // FP32 pair kernel, where 1e-7 relative on sub-Angstrom fluctuations is far
+            // below the pair arithmetic's own rounding.
+            float acc = 0.0f;
+            for (int k = 1; k < P; ++k) acc = fmaf(Tsf[k * P + n], qf[base + k], acc);
+            const float x = (float)(qs[base] - anc) + acc;
+            A.pos_f[((size_t)d * A.N + s) * P + n] = x;
+            xr[t] = x;
+        } else {
+            double acc = 0.0;
+            for (int k = 0; k < P; ++k) acc = fma(Tsd[k * P + n], qs[base + k], acc);
+            A.pos_d[((size_t)d * A.N + s) * P + n] = acc;
+            xr[t] = (float)(acc - anc);
+        }
+    }
+    __syncthreads();
+    if (valid && d == 0) {
+        const int base = la * 3 * P;
+        const float x0 = xr[base + n], x1 = xr[base + P + n], x2 = xr[base + 2 * P + n];
+        dv = x0 * x0 + x1 * x1 + x2 * x2;
+    }
+    block_max_atomic(dv, A.dev_max);
+}
+
+struct ProjectArgs {
+    int N, P, apb;
+    double half_dt_acc;
+    const double* Fd;
+    const long long* Ffix;
+    const double* Tp;      // T[b][n] / sqrt(P)
+    const float* Tpf;
+    double* fmode;
+    double* Pm;
+    unsigned* status;
+    unsigned long long* step_ctr;
+};
+
+// f_n = (1/sqrt P) sum_b T_bn F_b (Eqs. (10)-(11)) and, with KICK, B(dt/2) P_n += dt/2 f_n.
+template <bool MIXED, bool KICK>
+__global__ void __launch_bounds__(BLOCK) k_project(ProjectArgs A) {
+    __shared__ double Fs[BLOCK];
+    __shared__ long long Fi[BLOCK];
+    __shared__ float Ff[BLOCK];
+    extern __shared__ unsigned char smem_raw[];
+    const int P = A.P;
+    float* Tsf = reinterpret_cast<float*>(smem_raw);
+    double* Tsd = reinterpret_cast<double*>(smem_raw);
+    const int t = threadIdx.x;
+    const int la = t / (3 * P), d = (t / P) % 3, n = t % P;
+    const int a = blockIdx.x * A.apb + la;
+    const bool valid = a < A.N;
+    const int idx = (a * 3 + d) * P + n;
+    for (int k = t; k < P * P; k += BLOCK) {
+        if (MIXED) Tsf[k] = A.Tpf[k];
+        else Tsd[k] = A.Tp[k];
+    }
+    if (valid) {
+        if (MIXED) {
+            const long long v = A.Ffix[idx];
+            Fi[t] = v;
+            Ff[t] = __ll2float_rn(v) * (1.0f / FIX_SCALE_F);   // one conversion per bead force
+        } else {
+            Fs[t] = A.Fd[idx];
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        const int base = la * 3 * P + d * P;
+        double f;
+        if (MIXED) {
+            if (n == 0) {   // f_0 = mean bead force: exact integer sum of the fixed-point forces
+                long long sum = 0;
+                for (int b = 0; b < P; ++b) sum += Fi[base + b];
+                f = (double)sum * (1.0 / (FIX_SCALE * (double)P));   // power of two: exact scaling
+            } else {
+                float acc = 0.0f;
+                for (int b = 0; b < P; ++b) acc = fmaf(Tsf[b * P + n], Ff[base + b], acc);
+                f = (double)acc;
+            }
+        } else {
+            double acc = 0.0;
+            for (int b = 0; b < P; ++b) acc = fma(Tsd[b * P + n], Fs[base + b], acc);
+            f = acc;
+        }
+        A.fmode[idx] = f;
+        if (KICK) {
+            const double p = A.Pm[idx] + A.half_dt_acc * f;
+            A.Pm[idx] = p;
+            if (!isfinite(p)) atomicOr(A.status, ST_NONFINITE);
+        }
+    }
+    if (KICK && blockIdx.x == 0 && t == 0) *A.step_ctr += 1ull;
+}
+
+__global__ void k_init_modes(int N, int P, uint64_t seed, double kT_acc, const double* pos0, const double* mass,
+                             const double* omega, double* Q, double* Pm) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * 3 * P) return;
+    const int n = idx % P, dof = idx / P, a = dof / 3;
+    const double m = mass[a];
+    const double zq = normal_f64(philox_draw(seed, (uint32_t)idx, 0ull, TAG_INIT_Q), 0);
+    const double zp = normal_f64(philox_draw(seed, (uint32_t)idx, 0ull, TAG_INIT_P), 0);
+    Q[idx] = (n == 0) ? pos0[dof] : sqrt(kT_acc / (m * omega[n] * omega[n])) * zq;
+    Pm[idx] = sqrt(m * kT_acc) * zp;
+}
+
+// Per-block partial sums of: spring, kinetic, centroid-virial sum (x_b - Q_0).F_b.
+__global__ void __launch_bounds__(BLOCK) k_estimators(int N, int P, int apb, const double* Q, const double* Pm,
+                                                      const double* mass, const double* omega, const double* Tm,
+                                                      const double* Fd, const long long* Ffix, double* partial) {
+    __shared__ double qs[BLOCK];
+    __shared__ double red[3][BLOCK];
+    const int t = threadIdx.x;
+    const int la = t / (3 * P), d = (t / P) % 3, n = t % P;
+    const int a = blockIdx.x * apb + la;
+    const bool valid = a < N;
+    const int idx = (a * 3 + d) * P + n;
+    double q = valid ? Q[idx] : 0.0;
+    qs[t] = q;
+    __syncthreads();
+    double spring = 0.0, kin = 0.0, vir = 0.0;
+    if (valid) {
+        const double m = mass[a];
+        const double p = Pm[idx];
+        spring = 0.5 * m * omega[n] * omega[n] * q * q / ACC;
+        kin = p * p / (2.0 * m) / ACC;
+        const int base = la * 3 * P + d * P;
+        double dev = 0.0;     // x_b - Q_0 for bead b = n
+        for (int k = 1; k < P; ++k) dev = fma(Tm[n * P + k], qs[base + k], dev);
+        const double F = Ffix ? (double)Ffix[idx] / FIX_SCALE : Fd[idx];
+        vir = dev * F;
+    }
+    red[0][t] = spring;
+    red[1][t] = kin;
+    red[2][t] = vir;
+    __syncthreads();
+    if (t < 3) {
+        double s = 0.0;
+        for (int k = 0; k < BLOCK; ++k) s += red[t][k];   // fixed order
+        partial[(size_t)t * gridDim.x + blockIdx.x] = s;  // component-major [3][blocks]
+    }
+}
+
+__global__ void k_beads_fp64(int N, int P, const double* Q, const double* Tm, double* out /*[P][N][3]*/) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * 3 * P) return;
+    const int b = idx % P, dof = idx / P;
+    const double* q = Q + (size_t)dof * P;
+    double acc = 0.0;
+    for (int k = 0; k < P; ++k) acc = fma(Tm[b * P + k], q[k], acc);
+    out[((size_t)b * N + dof / 3) * 3 + dof % 3] = acc;
+}
+
+size_t integrate_smem(int P, bool mixed) { return BLOCK * 16 + (size_t)P * P * (mixed ? 4 : 8); }
+
+}  // namespace
+
+void transfer_matrix_host(int P, std::vector<double>& T) {
+    // Real orthonormal DFT basis: columns are eigenvectors of circ(2,-1,...,-1) (Eq. (2)).
+    T.assign((size_t)P * P, 0.0);
+    const double pi = 3.141592653589793238462643383279502884;
+    for (int b = 0; b < P; ++b)
+        for (int n = 0; n < P; ++n) {
+            const double ph = 2.0 * pi * (double)((b * n) % P) / (double)P;
+            double v;
+            if (n == 0) v = 1.0 / sqrt((double)P);
+            else if (2 * n < P) v = sqrt(2.0 / P) * cos(ph);
+            else if (2 * n == P) v = ((b & 1) ? -1.0 : 1.0) / sqrt((double)P);
+            else v = sqrt(2.0 / P) * sin(ph);
+            T[(size_t)b * P + n] = v;
+        }
+}
+
+void mode_constants(qhp_system_s* s) {
+    const int P = s->P;
+    const double kT = KB * s->temperature;
+    const double dt = s->th.dt_fs * 1e-3;
+    const double pi = 3.141592653589793238462643383279502884;
+    ModeConsts& m = s->mc;
+    for (int n = 0; n < 64; ++n) {
+        if (n >= P) {
+            m.omega[n] = m.shear_a[n] = m.shear_b[n] = m.c1[n] = m.amp[n] = 0.0;
+            continue;
+        }
+        const double w = 2.0 * P * kT / HBAR * sin(pi * n / P);
+        m.omega[n] = w;
+        const double th = w * 0.5 * dt;
+        m.shear_a[n] = (n == 0) ? 0.0 : tan(0.5 * th) / w;
+        m.shear_b[n] = (n == 0) ? 0.0 : sin(th) * w;
+        double g = (n == 0) ? s->th.gamma0 : fmax(s->th.gamma0, w);
+        if (s->th.kind == QHP_THERMO_NVE) g = 0.0;
+        const double c1 = exp(-g * dt);
+        m.c1[n] = c1;
+        if (s->th.kind == QHP_THERMO_ADQTB) m.amp[n] = sqrt((1.0 - c1 * c1) * ACC);
+        else m.amp[n] = sqrt((1.0 - c1 * c1) * kT * ACC);
+    }
+    // per (atom type, mode) table with the mass folded in: no FP64 division on the device
+    s->mode_tab_host.assign((size_t)2 * P * MT_N, 0.0);
+    for (int ty = 0; ty < 2; ++ty) {
+        const double mass = ty == 0 ? s->ff.m_O : s->ff.m_H;
+        for (int n = 0; n < P; ++n) {
+            double* c = &s->mode_tab_host[((size_t)ty * P + n) * MT_N];
+            c[MT_SA] = (n == 0) ? 0.5 * dt / mass : m.shear_a[n] / mass;
+            c[MT_SB] = m.shear_b[n] * mass;
+            c[MT_C1] = m.c1[n];
+            c[MT_AMP] = m.amp[n] * sqrt(mass);
+            c[MT_INV2M] = 0.5 / mass;
+        }
+    }
+}
+
+static IntegrateArgs make_iargs(qhp_system_s* s) {
+    IntegrateArgs A;
+    A.N = s->N;
+    A.P = s->P;
+    A.apb = 64 / s->P;
+    A.n_seg = s->n_seg > 0 ? s->n_seg : 1;
+    const double dt = s->th.dt_fs * 1e-3;
+    A.half_dt_acc = 0.5 * dt * ACC;
+    A.inv_dt = 1.0 / dt;
+    A.seed = s->seed;
+    A.step_ctr = s->step_ctr;
+    A.Q = s->Q;
+    A.Pm = s->Pm;
+    A.fmode = s->fmode;
+    A.type = s->type_d;
+    A.tab = s->mode_tab;
+    A.anchor = s->anchor;
+    A.iperm = s->iperm;
+    A.Tm = s->Tmat;
+    A.Tmf = s->Tmat_f;
+    A.pos_f = s->pos_f;
+    A.pos_d = s->pos_d;
+    A.dev_max = s->dev_max;
+    A.qtb_u = s->qtb_u;
+    A.qtb_v = s->qtb_v;
+    A.qtb_F = s->qtb_F;
+    A.gate = nullptr;
+    return A;
+}
+
+cudaError_t launch_integrate_gated(qhp_system_s* s) {
+    IntegrateArgs A = make_iargs(s);
+    A.gate = s->rebuild_flag;
+    const int grid = (s->N + A.apb - 1) / A.apb;
+    const bool mixed = s->precision == QHP_MIXED;
+    const size_t sm = integrate_smem(s->P, mixed);
+    s->launches++;
+    if (mixed) k_integrate<true, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+    else k_integrate<false, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(qhp_system_s* s, bool integrate, bool adqtb) {
+    IntegrateArgs A = make_iargs(s);
+    const int grid = (s->N + A.apb - 1) / A.apb;
+    const bool mixed = s->precision == QHP_MIXED;
+    const size_t sm = integrate_smem(s->P, mixed);
+    s->launches++;
+    if (mixed) {
+        if (!integrate) k_integrate<true, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+        else if (adqtb) k_integrate<true, true, true><<<grid, BLOCK, sm, s->stream>>>(A);
+        else k_integrate<true, false, true><<<grid, BLOCK, sm, s->stream>>>(A);
+    } else {
+        if (!integrate) k_integrate<false, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+        else if (adqtb) k_integrate<false, true, true><<<grid, BLOCK, sm, s->stream>>>(A);
+        else k_integrate<false, false, true><<<grid, BLOCK, sm, s->stream>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(qhp_system_s* s, bool kick) {
+    ProjectArgs A;
+    A.N = s->N;
+    A.P = s->P;
+    A.apb = 64 / s->P;
+    A.half_dt_acc = 0.5 * s->th.dt_fs * 1e-3 * ACC;
+    A.Fd = s->Fd;
+    A.Ffix = s->Ffix;
+    A.Tp = s->Tproj;
+    A.Tpf = s->Tproj_f;
+    A.fmode = s->fmode;
+    A.Pm = s->Pm;
+    A.status = s->status;
+    A.step_ctr = s->step_ctr;
+    const int grid = (s->N + A.apb - 1) / A.apb;
+    const bool mixed = s->precision == QHP_MIXED;
+    const size_t sm = (size_t)s->P * s->P * (mixed ? 4 : 8);
+    s->launches++;
+    if (mixed) {
+        if (kick) k_project<true, true><<<grid, BLOCK, sm, s->stream>>>(A);
+        else k_project<true, false><<<grid, BLOCK, sm, s->stream>>>(A);
+    } else {
+        if (kick) k_project<false, true><<<grid, BLOCK, sm, s->stream>>>(A);
+        else k_project<false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_modes(qhp_system_s* s) {
+    const int total = s->N * 3 * s->P;
+    double* omega_d = s->red_out;   // scratch: the first 64 doubles of red_out hold omega_n
+    cudaError_t e = cudaMemcpyAsync(omega_d, s->mc.omega, sizeof(double) * 64, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return e;
+    s->launches++;
+    // the initial positions are staged in the anchor buffer by the caller
+    k_init_modes<<<(total + 255) / 256, 256, 0, s->stream>>>(s->N, s->P, s->seed, KB * s->temperature * ACC,
+                                                             s->anchor, s->mass, omega_d, s->Q, s->Pm);
+    return cudaGetLastError();
+}
+
+int beads_fp64(qhp_system_s* s, double* dev_out) {
+    const int total = s->N * 3 * s->P;
+    s->launches++;
+    k_beads_fp64<<<(total + 255) / 256, 256, 0, s->stream>>>(s->N, s->P, s->Q, s->Tmat, dev_out);
+    QHP_CUDA(cudaGetLastError());
+    return QHP_OK;
+}
+
+cudaError_t launch_estimators(qhp_system_s* s, double* partial, int* nblocks) {
+    const int apb = 64 / s->P;
+    const int grid = (s->N + apb - 1) / apb;
+    *nblocks = grid;
+    double* omega_d = s->red_out + 64;
+    cudaError_t e = cudaMemcpyAsync(omega_d, s->mc.omega, sizeof(double) * 64, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return e;
+    s->launches++;
+    k_estimators<<<grid, BLOCK, 0, s->stream>>>(s->N, s->P, apb, s->Q, s->Pm, s->mass, omega_d, s->Tmat, s->Fd,
+                                                s->precision == QHP_MIXED ? s->Ffix : nullptr, partial);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_gather_centroids(int n3, int P, const double* __restrict__ Q, double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n3) out[k] = Q[(size_t)k * P];
+}
+}  // namespace
+
+// Centroids Q_0 into a contiguous [N][3] device buffer.
+cudaError_t launch_gather_centroids(qhp_system_s* s, double* out) {
+    const int n3 = 3 * s->N;
+    s->launches++;
+    k_gather_centroids<<<(n3 + 255) / 256, 256, 0, s->stream>>>(n3, s->P, s->Q, out);
+    return cudaGetLastError();
+}
+
+}  // namespace qhp

@@ -1,0 +1,363 @@
+// Centroid cell grid, counting sort and Verlet list (Sec. III.A.3: one list on
+// ring-polymer centroids serves every bead).
+//
+// Every kernel of the rebuild chain reads the device rebuild flag first and
+// returns at once when it is clear, so the chain can sit inside a captured
+// CUDA graph that replays every step.
+//
+// Bit-exactness with the definition: the cell of a centroid C is
+//   t = C/L, frac = t - floor(t) (0 if it rounds to 1), c = min(floor(frac n_c), n_c - 1),
+// and (i, j) is listed iff molecules differ and
+//   d = C_j - C_i - L rint((C_j - C_i)/L), (dx*dx + dy*dy) + dz*dz < r_list^2,
+// with each operation rounded on its own (explicit _rn intrinsics, no FMA).  An
+// FP32 prefilter on wrapped centroids decides the candidates that are more than
+// 1e-3 A away from r_list; the rest get the exact FP64 test above.
+#include "qhp_internal.cuh"
+
+namespace qhp {
+
+namespace {
+
+__device__ __forceinline__ double min_image_rn(double d, double L) {
+    return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+}
+
+__device__ __forceinline__ int cell_coord(double C, double L, int n_c, double* frac_out) {
+    const double t = __ddiv_rn(C, L);
+    double frac = __dsub_rn(t, floor(t));
+    if (frac == 1.0) frac = 0.0;
+    *frac_out = frac;
+    int c = (int)floor(__dmul_rn(frac, (double)n_c));
+    return c < n_c - 1 ? c : n_c - 1;
+}
+
+// Clear the cell counters and the deviation maximum if a rebuild is due.
+__global__ void k_check(unsigned* dev_max, float thr2, int* flag, int force, unsigned* rebuild_count,
+                        const unsigned* status) {
+    const float dmax = __uint_as_float(*dev_max);
+    const int rebuild = force || !(dmax <= thr2);   // NaN also triggers a rebuild
+    *flag = rebuild;
+    if (rebuild) {
+        *dev_max = 0u;
+        *rebuild_count += 1u;
+    }
+}
+
+__global__ void k_zero_ints(const int* flag, int* a, int n) {
+    if (!*flag) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 0;
+}
+
+// New anchors = current centroids Q_0 (or, with keep, the stored anchors of a
+// checkpoint); cell of every atom (list mode).
+__global__ void k_cells(const int* flag, int N, int P, const double* Q, double L, int n_c, int list_mode,
+                        double* anchor, int* cell, int* cell_count, int keep) {
+    if (!*flag) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= N) return;
+    int c3[3];
+    for (int d = 0; d < 3; ++d) {
+        const double C = keep ? anchor[a * 3 + d] : Q[((size_t)a * 3 + d) * P];
+        if (!keep) anchor[a * 3 + d] = C;
+        double fr;
+        c3[d] = cell_coord(C, L, n_c, &fr);
+    }
+    if (list_mode) {
+        const int c = (c3[2] * n_c + c3[1]) * n_c + c3[0];
+        cell[a] = c;
+        atomicAdd(&cell_count[c], 1);
+    }
+}
+
+// Exclusive scan of n values (single block of 1024 threads).
+__global__ void k_scan(const int* flag, const int* in, int* out, int n, int64_t cap, int* total, unsigned* status) {
+    if (!*flag) return;
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        int v = i < n ? in[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = warp_sums[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int excl = carry + x - v + (w > 0 ? warp_sums[w - 1] : 0);
+        if (i < n) out[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[n] = carry;
+        if (total) *total = carry;
+        if (cap >= 0 && (int64_t)carry > cap) atomicOr(status, ST_LIST_OVERFLOW);
+    }
+}
+
+__global__ void k_cell_scatter(const int* flag, int N, const int* cell, const int* cell_start, int* cell_fill,
+                               int* tmp) {
+    if (!*flag) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= N) return;
+    const int c = cell[a];
+    const int slot = atomicAdd(&cell_fill[c], 1);
+    tmp[cell_start[c] + slot] = a;
+}
+
+// Order each cell's atoms by index: rank = number of smaller indices in the cell.
+__global__ void k_cell_sort(const int* flag, const int* cell_start, const int* tmp, int* perm, int* iperm) {
+    if (!*flag) return;
+    const int c = blockIdx.x;
+    const int s0 = cell_start[c], s1 = cell_start[c + 1];
+    for (int e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
+        const int a = tmp[e];
+        int rank = 0;
+        for (int k = s0; k < s1; ++k) rank += tmp[k] < a;
+        perm[s0 + rank] = a;
+        iperm[a] = s0 + rank;
+    }
+}
+
+__global__ void k_identity_order(const int* flag, int N, int* perm, int* iperm) {
+    if (!*flag) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= N) return;
+    perm[a] = a;
+    iperm[a] = a;
+}
+
+// Sorted per-atom attributes, FP32 wrapped centroids and (mixed) intramolecular anchor offsets.
+__global__ void k_sorted_attrs(const int* flag, int N, double L, const int* perm, const int* type, const int* mol,
+                               const double* anchor, float q_O, float q_H, float* charge_s, int* type_s, int* mol_s,
+                               float4* cw, float* dA) {
+    if (!*flag) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const int a = perm[s];
+    const int ty = type[a];
+    charge_s[s] = ty == 0 ? q_O : q_H;
+    type_s[s] = ty;
+    mol_s[s] = mol[a];
+    double w[3];
+    for (int d = 0; d < 3; ++d) {   // wrapped coordinate frac * L, consistent with the cell index
+        double fr;
+        (void)cell_coord(anchor[a * 3 + d], L, 1, &fr);
+        w[d] = fr * L;
+    }
+    cw[s] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.0f);
+    if (dA && (a % 3) != 0) {     // H atom: min-image A_H - A_O of its molecule
+        const int o = a - (a % 3);
+        float* out = dA + ((size_t)(a / 3) * 2 + (a % 3) - 1) * 4;
+        for (int d = 0; d < 3; ++d) out[d] = (float)min_image_rn(anchor[a * 3 + d] - anchor[o * 3 + d], L);
+        out[3] = 0.0f;
+    }
+}
+
+// Centroid Verlet list, warp per sorted atom i; FILL = false counts, true writes entries.
+template <bool FILL>
+__global__ void k_list(const int* flag, int N, double L, int n_c, double r2max, float lo2, float hi2,
+                       const int* perm, const int* cell, const int* cell_start, const float4* cw, const int* mol_s,
+                       const int* type_s, const double* anchor, int* count, const int* start, int4* nbr, int64_t cap) {
+    if (!*flag) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    const int ai = perm[i];
+    const int ci = cell[ai];
+    const int cx = ci % n_c, cy = (ci / n_c) % n_c, cz = ci / (n_c * n_c);
+    const float4 wi = cw[i];
+    const int mi = mol_s[i];
+    const double Ci0 = anchor[ai * 3], Ci1 = anchor[ai * 3 + 1], Ci2 = anchor[ai * 3 + 2];
+    const float Lf = (float)L;
+    int cnt = 0;
+    const int base = FILL ? start[i] : 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = cx + dx, y = cy + dy, z = cz + dz;
+                float sx = 0.f, sy = 0.f, sz = 0.f;
+                if (x < 0) { x += n_c; sx = -Lf; } else if (x >= n_c) { x -= n_c; sx = Lf; }
+                if (y < 0) { y += n_c; sy = -Lf; } else if (y >= n_c) { y -= n_c; sy = Lf; }
+                if (z < 0) { z += n_c; sz = -Lf; } else if (z >= n_c) { z -= n_c; sz = Lf; }
+                const int cj = (z * n_c + y) * n_c + x;
+                const int j0 = cell_start[cj], j1 = cell_start[cj + 1];
+                for (int jb = j0; jb < j1; jb += 32) {
+                    const int j = jb + lane;
+                    bool acc = false;
+                    if (j < j1 && mol_s[j] != mi) {
+                        const float4 wj = cw[j];
+                        const float ddx = (wj.x + sx) - wi.x, ddy = (wj.y + sy) - wi.y, ddz = (wj.z + sz) - wi.z;
+                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        if (r2 < lo2) {
+                            acc = true;
+                        } else if (r2 <= hi2) {
+                            const int aj = perm[j];
+                            const double ex = min_image_rn(__dsub_rn(anchor[aj * 3], Ci0), L);
+                            const double ey = min_image_rn(__dsub_rn(anchor[aj * 3 + 1], Ci1), L);
+                            const double ez = min_image_rn(__dsub_rn(anchor[aj * 3 + 2], Ci2), L);
+                            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                            acc = d2 < r2max;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, acc);
+                    if (FILL && acc) {
+                        const int64_t pos = (int64_t)base + cnt + __popc(bal & ((1u << lane) - 1u));
+                        if (pos < cap) {
+                            const int aj = perm[j];
+                            const float Dx = (float)min_image_rn(anchor[aj * 3] - Ci0, L);
+                            const float Dy = (float)min_image_rn(anchor[aj * 3 + 1] - Ci1, L);
+                            const float Dz = (float)min_image_rn(anchor[aj * 3 + 2] - Ci2, L);
+                            nbr[pos] = make_int4(j | (type_s[j] ? (int)0x80000000u : 0), __float_as_int(Dx),
+                                                 __float_as_int(Dy), __float_as_int(Dz));
+                        }
+                    }
+                    cnt += __popc(bal);
+                }
+            }
+    if (!FILL && lane == 0) count[i] = cnt;
+}
+
+// All pairs of different molecules (small boxes), warp per atom, identity order.
+template <bool FILL>
+__global__ void k_list_all(const int* flag, int N, double L, const int* mol_s, const int* type_s, const double* anchor,
+                           int* count, const int* start, int4* nbr, int64_t cap) {
+    if (!*flag) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    const int mi = mol_s[i];
+    int cnt = 0;
+    const int base = FILL ? start[i] : 0;
+    for (int jb = 0; jb < N; jb += 32) {
+        const int j = jb + lane;
+        const bool acc = j < N && mol_s[j] != mi;
+        const unsigned bal = __ballot_sync(0xffffffffu, acc);
+        if (FILL && acc) {
+            const int64_t pos = (int64_t)base + cnt + __popc(bal & ((1u << lane) - 1u));
+            if (pos < cap) {
+                const float Dx = (float)min_image_rn(anchor[j * 3] - anchor[i * 3], L);
+                const float Dy = (float)min_image_rn(anchor[j * 3 + 1] - anchor[i * 3 + 1], L);
+                const float Dz = (float)min_image_rn(anchor[j * 3 + 2] - anchor[i * 3 + 2], L);
+                nbr[pos] = make_int4(j | (type_s[j] ? (int)0x80000000u : 0), __float_as_int(Dx), __float_as_int(Dy),
+                                     __float_as_int(Dz));
+            }
+        }
+        cnt += __popc(bal);
+    }
+    if (!FILL && lane == 0) count[i] = cnt;
+}
+
+}  // namespace
+
+cudaError_t launch_list_check(qhp_system_s* s, bool force) {
+    const float half = (float)(0.5 * s->ff.skin);
+    s->launches++;
+    k_check<<<1, 1, 0, s->stream>>>(s->dev_max, half * half, s->rebuild_flag, force ? 1 : 0, s->rebuild_count,
+                                    s->status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(qhp_system_s* s) {
+    const int N = s->N;
+    const int tb = 256, gN = (N + tb - 1) / tb;
+    const int ncell = s->n_c * s->n_c * s->n_c;
+    const int* flag = s->rebuild_flag;
+    cudaStream_t st = s->stream;
+    if (s->list_mode) {
+        k_zero_ints<<<(ncell + tb - 1) / tb, tb, 0, st>>>(flag, s->cell_count, ncell);
+        k_zero_ints<<<(ncell + tb - 1) / tb, tb, 0, st>>>(flag, s->cell_fill, ncell);
+        k_cells<<<gN, tb, 0, st>>>(flag, N, s->P, s->Q, s->L, s->n_c, 1, s->anchor, s->cell, s->cell_count,
+                                   s->keep_anchor);
+        k_scan<<<1, 1024, 0, st>>>(flag, s->cell_count, s->cell_start, ncell, -1, nullptr, s->status);
+        k_cell_scatter<<<gN, tb, 0, st>>>(flag, N, s->cell, s->cell_start, s->cell_fill, s->tmp_idx);
+        k_cell_sort<<<ncell, 128, 0, st>>>(flag, s->cell_start, s->tmp_idx, s->perm, s->iperm);
+        s->launches += 6;
+    } else {
+        k_cells<<<gN, tb, 0, st>>>(flag, N, s->P, s->Q, s->L, 1, 0, s->anchor, nullptr, nullptr, s->keep_anchor);
+        k_identity_order<<<gN, tb, 0, st>>>(flag, N, s->perm, s->iperm);
+        s->launches += 2;
+    }
+    k_sorted_attrs<<<gN, tb, 0, st>>>(flag, N, s->L, s->perm, s->type_d, s->mol_d, s->anchor, (float)s->ff.q_O,
+                                      (float)(-0.5 * s->ff.q_O), s->charge_s, s->type_s, s->mol_s, s->cw,
+                                      s->precision == QHP_MIXED ? s->dA : nullptr);
+    const int wb = 128, gW = (N * 32 + wb - 1) / wb;
+    const double r2max = s->r_list * s->r_list;
+    const float lo = (float)(s->r_list - 1e-3), hi = (float)(s->r_list + 1e-3);
+    if (s->list_mode) {
+        k_list<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
+                                         s->cell_start, s->cw, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+    } else {
+        k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+    }
+    k_scan<<<1, 1024, 0, st>>>(flag, s->nbr_count, s->nbr_start, N, s->nbr_cap, s->nbr_total, s->status);
+    if (s->list_mode) {
+        k_list<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
+                                        s->cell_start, s->cw, s->mol_s, s->type_s, s->anchor, nullptr, s->nbr_start, s->nbr,
+                                        s->nbr_cap);
+    } else {
+        k_list_all<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, nullptr, s->nbr_start, s->nbr,
+                                            s->nbr_cap);
+    }
+    s->launches += 4;
+    return cudaGetLastError();
+}
+
+// Count the list entries for the current centroids (synchronous; sizes the buffer).
+int host_list_size(qhp_system_s* s, int64_t* total) {
+    int one = 1;
+    QHP_CUDA(cudaMemcpyAsync(s->rebuild_flag, &one, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    const int N = s->N;
+    const int tb = 256, gN = (N + tb - 1) / tb;
+    const int ncell = s->n_c * s->n_c * s->n_c;
+    const int* flag = s->rebuild_flag;
+    cudaStream_t st = s->stream;
+    if (s->list_mode) {
+        k_zero_ints<<<(ncell + tb - 1) / tb, tb, 0, st>>>(flag, s->cell_count, ncell);
+        k_zero_ints<<<(ncell + tb - 1) / tb, tb, 0, st>>>(flag, s->cell_fill, ncell);
+        k_cells<<<gN, tb, 0, st>>>(flag, N, s->P, s->Q, s->L, s->n_c, 1, s->anchor, s->cell, s->cell_count,
+                                   s->keep_anchor);
+        k_scan<<<1, 1024, 0, st>>>(flag, s->cell_count, s->cell_start, ncell, -1, nullptr, s->status);
+        k_cell_scatter<<<gN, tb, 0, st>>>(flag, N, s->cell, s->cell_start, s->cell_fill, s->tmp_idx);
+        k_cell_sort<<<ncell, 128, 0, st>>>(flag, s->cell_start, s->tmp_idx, s->perm, s->iperm);
+    } else {
+        k_cells<<<gN, tb, 0, st>>>(flag, N, s->P, s->Q, s->L, 1, 0, s->anchor, nullptr, nullptr, s->keep_anchor);
+        k_identity_order<<<gN, tb, 0, st>>>(flag, N, s->perm, s->iperm);
+    }
+    k_sorted_attrs<<<gN, tb, 0, st>>>(flag, N, s->L, s->perm, s->type_d, s->mol_d, s->anchor, (float)s->ff.q_O,
+                                      (float)(-0.5 * s->ff.q_O), s->charge_s, s->type_s, s->mol_s, s->cw,
+                                      s->precision == QHP_MIXED ? s->dA : nullptr);
+    const int wb = 128, gW = (N * 32 + wb - 1) / wb;
+    const double r2max = s->r_list * s->r_list;
+    const float lo = (float)(s->r_list - 1e-3), hi = (float)(s->r_list + 1e-3);
+    if (s->list_mode)
+        k_list<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
+                                         s->cell_start, s->cw, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+    else
+        k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+    k_scan<<<1, 1024, 0, st>>>(flag, s->nbr_count, s->nbr_start, N, -1, s->nbr_total, s->status);
+    s->launches += 10;
+    QHP_CUDA(cudaGetLastError());
+    int t = 0;
+    QHP_CUDA(cudaMemcpyAsync(&t, s->nbr_total, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    QHP_CUDA(cudaStreamSynchronize(s->stream));
+    *total = t;
+    return QHP_OK;
+}
+
+}  // namespace qhp

@@ -1,0 +1,255 @@
+// Internal declarations of the qhp library: system state, device helpers, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qhp.h"
+
+namespace qhp {
+
+// ------------------------------------------------------------------ units
+// kcal/mol, Angstrom, amu, ps.  ACC converts (kcal/mol)/amu to A^2/ps^2.
+constexpr double ACC = 418.4;
+constexpr double KB = 8.314462618 / 4184.0;                           // kcal/mol/K
+constexpr double HBAR = 1.054571817e-34 * 6.02214076e23 / 4184.0 * 1e12;  // kcal/mol*ps
+constexpr double COULOMB = 332.0637133;                                // kcal*A/(mol e^2)
+constexpr double CM1 = 2.0 * 3.141592653589793 * 2.99792458e10 * 1e-12;  // cm^-1 -> rad/ps
+// Fixed-point scale of mixed-precision bead forces (kcal/mol/A): 2^34.
+constexpr double FIX_SCALE = 17179869184.0;
+constexpr float FIX_SCALE_F = 17179869184.0f;
+
+// Device status word bits.
+enum : unsigned {
+    ST_LIST_OVERFLOW = 1u,
+    ST_NONFINITE = 2u,
+    ST_TIMEOUT = 4u,
+};
+
+// Philox4x32-10 counter tags (same definition as the oracle, written independently).
+enum : uint32_t { TAG_INIT_Q = 1, TAG_INIT_P = 2, TAG_OSTEP = 3, TAG_QTB_WHITE = 4 };
+
+// ------------------------------------------------------------------ Philox
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// Salmon et al., SC'11: ten rounds, multipliers 0xD2511F53 / 0xCD9E8D57,
+// Weyl key increments 0x9E3779B9 / 0xBB67AE85 between rounds.
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox_draw(uint64_t seed, uint32_t elem, uint64_t step, uint32_t tag) {
+    return philox10(make_uint4(elem, (uint32_t)step, (uint32_t)(step >> 32), tag), (uint32_t)seed,
+                    (uint32_t)(seed >> 32));
+}
+
+// 53-bit integer k = (hi >> 5) * 2^26 + (lo >> 6); the uniform is (k + 1/2) 2^-53.
+__device__ __forceinline__ uint64_t bits53(uint32_t hi, uint32_t lo) {
+    return ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
+}
+
+// Box-Muller in FP64: which = 0 -> r cos(2 pi u2), 1 -> r sin(2 pi u2).
+__device__ __forceinline__ double normal_f64(uint4 x, int which) {
+    const double u1 = ((double)bits53(x.x, x.y) + 0.5) * 0x1p-53;
+    const double u2 = ((double)bits53(x.z, x.w) + 0.5) * 0x1p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    return which ? r * s : r * c;
+}
+
+// Box-Muller in FP32 on the same 53-bit integers: the uniform keeps 24-bit
+// *relative* precision down to 2^-54, so log(u1) stays accurate in the tail.
+__device__ __forceinline__ float normal_f32(uint4 x, int which) {
+    const float u1 = __fmaf_rn(__ull2float_rn(bits53(x.x, x.y)), 0x1p-53f, 0x1p-54f);
+    const float u2 = __fmaf_rn(__ull2float_rn(bits53(x.z, x.w)), 0x1p-53f, 0x1p-54f);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return which ? r * s : r * c;
+}
+
+// ------------------------------------------------------------------ system
+struct ModeConsts {           // per-mode constants of one step, FP64
+    double omega[64];
+    double shear_a[64];       // tan(omega dt/4) / omega   (A(dt/2) shear, / m)
+    double shear_b[64];       // sin(omega dt/2) * omega   (A(dt/2) shear, * m)
+    double c1[64];            // exp(-gamma_n dt)
+    double amp[64];           // sqrt((1 - c1^2) kT ACC)    (* sqrt(m))
+};
+
+// Per (atom type, mode) constants of the integrator, mass folded in.
+enum : int {
+    MT_SA = 0,      // shear a / m (centroid: dt/2 / m drift)
+    MT_SB = 1,      // shear b * m
+    MT_C1 = 2,      // exp(-gamma_n dt)
+    MT_AMP = 3,     // sqrt((1 - c1^2) m kT) (PILE) or sqrt((1 - c1^2) m) (adQTB), A^2/ps^2 units
+    MT_INV2M = 4,   // 1 / (2 m)
+    MT_N = 8
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace qhp
+
+struct qhp_system_s {
+    // ---- configuration
+    int N = 0, n_mol = 0, P = 0, precision = QHP_MIXED;
+    double L = 0.0;
+    std::vector<int> type, mol;
+    std::vector<double> pos0;
+    qhp_ff ff{};
+    bool ff_set = false, beads_set = false, thermo_set = false;
+    qhp_thermo th{};
+    double temperature = 300.0;
+    uint64_t seed = 0;
+    int list_mode = 0;         // 1: centroid Verlet list, 0: all pairs of different molecules
+    int n_c = 1;               // cells per edge
+    double r_list = 0.0;
+
+    // ---- CUDA
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t launches = 0;
+
+    // ---- device state (original atom order unless marked "sorted")
+    double *Q = nullptr, *Pm = nullptr, *fmode = nullptr;    // [N][3][P]
+    double *Fd = nullptr;                                    // FP64 bead forces [N][3][P]
+    long long* Ffix = nullptr;                               // mixed bead forces, fixed point [N][3][P]
+    float* pos_f = nullptr;                                  // mixed: sorted [3][N][P], x - anchor
+    double* pos_d = nullptr;                                 // fp64: sorted [3][N][P], absolute
+    double* anchor = nullptr;                                // [N][3] centroids at the last build
+    float* dA = nullptr;                                     // mixed: [n_mol][2][4] min-image A_H - A_O
+    double* mass = nullptr;                                  // [N]
+    double* sqrtm = nullptr;                                 // [N]
+    float* charge_s = nullptr;                               // sorted charges
+    int* type_s = nullptr;                                   // sorted types
+    int* mol_s = nullptr;                                    // sorted molecule ids
+    int* mol_d = nullptr;                                    // [N] molecule id
+    int* type_d = nullptr;                                   // [N]
+    int *perm = nullptr, *iperm = nullptr;                   // sorted -> atom, atom -> sorted
+    int *cell = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr, *tmp_idx = nullptr;
+    float4* cw = nullptr;                                    // sorted wrapped centroids (FP32) for the prefilter
+    int* nbr_start = nullptr;                                // [N+1]
+    int* nbr_count = nullptr;                                // [N]
+    int4* nbr = nullptr;                                     // entries {j, Dx, Dy, Dz}
+    int64_t nbr_cap = 0;
+    float* e_pair = nullptr;                                 // per (sorted atom, bead) pair energy (mixed)
+    double* e_pair_d = nullptr;                              // fp64
+    double* e_bond = nullptr;                                // [n_mol][P]
+    double* red_tmp = nullptr;                               // reduction scratch
+    double* red_out = nullptr;                               // reduction results
+    unsigned* status = nullptr;                              // device status word
+    unsigned* status_host = nullptr;                         // pinned copy, refreshed after each step call
+    cudaEvent_t status_event = nullptr;
+    unsigned* dev_max = nullptr;                             // max squared deviation (float bits)
+    int* rebuild_flag = nullptr;
+    int* nbr_total = nullptr;
+    unsigned long long* step_ctr = nullptr;                  // device copy of the step counter
+    int64_t rebuilds_host = 0;
+    int keep_anchor = 0;           // 1 while a checkpoint restore rebuilds from stored anchors
+    int prof_on = 0;               // per-stage events recorded inside each step
+    cudaEvent_t prof_ev[6] = {};
+    double* cent_buf = nullptr;    // [N][3] centroid gather buffer
+    unsigned* rebuild_count = nullptr;
+
+    // ---- adQTB
+    int n_seg = 0;
+    float* qtb_u = nullptr;        // [n_seg][3N]
+    float* qtb_v = nullptr;        // [n_seg][3N]
+    float* qtb_F = nullptr;        // [n_seg][3N]
+    double* qtb_gamma = nullptr;   // [2][n_seg+1]
+    double* qtb_sqrtS = nullptr;   // [2][n_seg+1] sqrt of the noise power
+    double* qtb_h = nullptr;       // [2][2 n_seg] filter taps
+    float2* qtb_H = nullptr;       // [2][4 n_seg] filter transform
+    float2* qtb_tw4 = nullptr;     // FFT twiddles, 4 n_seg points
+    float2* qtb_tw2 = nullptr;     // FFT twiddles, 2 n_seg points
+    int* qtb_dof_type = nullptr;   // [3N]
+    double* qtb_mdof = nullptr;    // [3N]
+    double* qtb_avg = nullptr;     // RATIO running averages [2][2][n_seg+1]
+    double* qtb_part = nullptr;    // spectra partial sums
+    double* qtb_delta = nullptr;   // last delta bar [2][n_seg+1]
+    int qtb_ratio_first = 1;
+
+    // ---- step constants
+    qhp::ModeConsts mc{};
+    std::vector<double> mode_tab_host;   // [2][P][MT_N]
+    double* mode_tab = nullptr;
+    double* Tmat = nullptr;        // sqrt(P) T[b][n], FP64 [P][P]
+    float* Tmat_f = nullptr;       // same, FP32
+    double* Tproj = nullptr;       // T[b][n] / sqrt(P), FP64
+    float* Tproj_f = nullptr;
+
+    double* est_part = nullptr;    // estimator partial sums [3][blocks]
+    double fdt_delta_last = 0.0;
+
+    // ---- state bookkeeping
+    int64_t kernels_per_step = 0;
+    int64_t step = 0;              // host mirror of the device step counter
+    bool forces_valid = false;
+    bool list_valid = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_kind = -1;
+
+    std::vector<qhp::DevBuf> allocs;
+};
+
+namespace qhp {
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define QHP_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return ::qhp::cuda_fail(e_, #call);  \
+    } while (0)
+
+// ---- kernels (launchers return cudaError_t of the launch)
+struct StepArgs;
+
+cudaError_t launch_init_modes(qhp_system_s* s);
+cudaError_t launch_integrate(qhp_system_s* s, bool integrate, bool adqtb);
+cudaError_t launch_integrate_gated(qhp_system_s* s);   // positions only, if the rebuild flag is set
+int qtb_setup(qhp_system_s* s);
+cudaError_t launch_project(qhp_system_s* s, bool kick);
+cudaError_t launch_list_check(qhp_system_s* s, bool force);
+cudaError_t launch_rebuild(qhp_system_s* s);
+cudaError_t launch_forces(qhp_system_s* s, bool energy);
+cudaError_t launch_pair(qhp_system_s* s, bool energy);
+cudaError_t launch_bonded(qhp_system_s* s, bool energy);
+cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2);
+cudaError_t launch_gather_centroids(qhp_system_s* s, double* out);
+cudaError_t launch_step_counter(qhp_system_s* s);
+int host_list_size(qhp_system_s* s, int64_t* total);
+int compute_energy(qhp_system_s* s, qhp_energy* out);
+int beads_fp64(qhp_system_s* s, double* dev_out);
+cudaError_t launch_estimators(qhp_system_s* s, double* partial, int* nblocks);
+cudaError_t launch_sum(qhp_system_s* s, const double* xd, const float* xf, int64_t n, double* out);
+cudaError_t launch_qtb_segment_end(qhp_system_s* s);     // spectra, adaptation, next filter
+int qtb_generate_segment(qhp_system_s* s, int64_t seg);  // colored noise of segment seg
+
+void mode_constants(qhp_system_s* s);
+void transfer_matrix_host(int P, std::vector<double>& T);  // T[b*P + n]
+
+}  // namespace qhp

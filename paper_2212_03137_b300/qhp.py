@@ -1,0 +1,381 @@
+"""Thin ctypes binding of the C ABI in ``include/qhp.h`` (argument marshalling only).
+
+Every function mirrors the C entry point of the same name; a nonzero return
+code raises :class:`QHPError` carrying ``qhp_last_error()``.  Host arrays are
+numpy; the ``_device`` variants take torch CUDA tensors (their data_ptr()).
+There is no CPU fallback: if ``libqhp.so`` is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqhp.so")
+
+QHP_OK = 0
+ERRORS = {-1: "QHP_ERR_ARG", -2: "QHP_ERR_CUDA", -3: "QHP_ERR_TIMEOUT", -4: "QHP_ERR_NONFINITE",
+          -5: "QHP_ERR_LIST_OVERFLOW", -6: "QHP_ERR_STATE", -7: "QHP_ERR_NOMEM"}
+QHP_FP64, QHP_MIXED = 0, 1
+QHP_THERMO_PILE, QHP_THERMO_ADQTB, QHP_THERMO_NVE = 0, 1, 2
+QHP_ADAPT_NONE, QHP_ADAPT_SIMPLE, QHP_ADAPT_RATIO = 0, 1, 2
+
+
+class QHPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qhp_ff(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("eps", "sigma", "q_O", "k_b", "r0", "k_theta", "theta0",
+                                          "alpha", "rc", "skin", "m_O", "m_H")]
+
+
+class qhp_thermo(C.Structure):
+    _fields_ = [("kind", C.c_int), ("gamma0", C.c_double), ("dt_fs", C.c_double), ("n_seg", C.c_int),
+                ("omega_cut_cm", C.c_double), ("a_gamma", C.c_double), ("gamma_min_frac", C.c_double),
+                ("adapt", C.c_int), ("tau_ratio_ps", C.c_double)]
+
+
+class qhp_energy(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("potential", "spring", "kinetic_nm", "kinetic_cv", "fdt_delta",
+                                          "bonded", "nonbonded", "reserved")]
+
+
+class qhp_info(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("P", C.c_int), ("precision", C.c_int), ("list_mode", C.c_int),
+                ("step", C.c_int64), ("rebuilds", C.c_int64), ("list_entries", C.c_int64),
+                ("list_capacity", C.c_int64), ("kernel_launches", C.c_int64),
+                ("n_cells_per_edge", C.c_int), ("reserved", C.c_int)]
+
+
+_lib = None
+_VP, _DP, _FP, _IP = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int)
+_SIGS = {
+    "qhp_create_system": [C.POINTER(C.c_void_p), C.c_int, _IP, _IP, _DP, C.c_double, C.c_int],
+    "qhp_destroy_system": [_VP],
+    "qhp_set_forcefield": [_VP, C.POINTER(qhp_ff)],
+    "qhp_set_beads": [_VP, C.c_int, C.c_double, C.c_uint64],
+    "qhp_set_thermostat": [_VP, C.POINTER(qhp_thermo)],
+    "qhp_step_rpmd": [_VP, C.c_int],
+    "qhp_step_adqtb": [_VP, C.c_int],
+    "qhp_compute_forces": [_VP],
+    "qhp_sync": [_VP],
+    "qhp_get_energy": [_VP, C.POINTER(qhp_energy)],
+    "qhp_get_forces": [_VP, _DP],
+    "qhp_get_centroid": [_VP, _DP],
+    "qhp_get_beads": [_VP, _DP],
+    "qhp_get_modes": [_VP, _DP, _DP],
+    "qhp_set_modes": [_VP, _DP, _DP],
+    "qhp_set_modes_device": [_VP, _VP, _VP],
+    "qhp_get_modes_device": [_VP, _VP, _VP],
+    "qhp_get_forces_device": [_VP, _VP],
+    "qhp_get_state": [_VP, _VP, C.POINTER(C.c_size_t)],
+    "qhp_set_state": [_VP, _VP, C.c_size_t],
+    "qhp_get_gamma": [_VP, _DP],
+    "qhp_set_gamma": [_VP, _DP],
+    "qhp_get_qtb_noise": [_VP, _FP],
+    "qhp_get_qtb_records": [_VP, _FP, _FP],
+    "qhp_build_list": [_VP],
+    "qhp_get_cells": [_VP, _IP, _IP],
+    "qhp_get_list_pairs": [_VP, C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64)],
+    "qhp_get_info": [_VP, C.POINTER(qhp_info)],
+    "qhp_set_stream": [_VP, _VP],
+    "qhp_set_profiling": [_VP, C.c_int],
+    "qhp_get_profile": [_VP, _VP],
+    "qhp_count_pairs": [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+}
+
+
+class qhp_profile(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("integrate_ms", "list_ms", "pair_ms", "bonded_ms", "project_ms",
+                                         "step_ms")]
+
+
+def lib():
+    """Load libqhp.so (raises if it was not built: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} missing (run paper_2212_03137_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.qhp_last_error.argtypes = []
+        L.qhp_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != QHP_OK:
+        raise QHPError(rc, lib().qhp_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _fp(a):
+    return a.ctypes.data_as(_FP)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_IP)
+
+
+# ------------------------------------------------------------------ C mirrors
+
+def qhp_create_system(types, molecule, pos, box, precision) -> C.c_void_p:
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    m = np.ascontiguousarray(molecule, dtype=np.int32)
+    p = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    h = C.c_void_p()
+    _check(lib().qhp_create_system(C.byref(h), int(len(t)), _ip(t), _ip(m), _dp(p), float(box), int(precision)))
+    return h
+
+
+def qhp_destroy_system(h) -> None:
+    _check(lib().qhp_destroy_system(h))
+
+
+def qhp_set_forcefield(h, ff: qhp_ff) -> None:
+    _check(lib().qhp_set_forcefield(h, C.byref(ff)))
+
+
+def qhp_set_beads(h, P: int, temperature: float, seed: int) -> None:
+    _check(lib().qhp_set_beads(h, int(P), float(temperature), int(seed)))
+
+
+def qhp_set_thermostat(h, th: qhp_thermo) -> None:
+    _check(lib().qhp_set_thermostat(h, C.byref(th)))
+
+
+def qhp_step_rpmd(h, n: int) -> None:
+    _check(lib().qhp_step_rpmd(h, int(n)))
+
+
+def qhp_step_adqtb(h, n: int) -> None:
+    _check(lib().qhp_step_adqtb(h, int(n)))
+
+
+def qhp_compute_forces(h) -> None:
+    _check(lib().qhp_compute_forces(h))
+
+
+def qhp_sync(h) -> None:
+    _check(lib().qhp_sync(h))
+
+
+def qhp_get_energy(h) -> qhp_energy:
+    e = qhp_energy()
+    _check(lib().qhp_get_energy(h, C.byref(e)))
+    return e
+
+
+def qhp_get_info(h) -> qhp_info:
+    i = qhp_info()
+    _check(lib().qhp_get_info(h, C.byref(i)))
+    return i
+
+
+def _dims(h):
+    i = qhp_get_info(h)
+    return i.n_atoms, i.P
+
+
+def qhp_get_forces(h, out=None) -> np.ndarray:
+    N, P = _dims(h)
+    out = np.empty((P, N, 3)) if out is None else out
+    _check(lib().qhp_get_forces(h, _dp(out)))
+    return out
+
+
+def qhp_get_centroid(h) -> np.ndarray:
+    N, _ = _dims(h)
+    out = np.empty((N, 3))
+    _check(lib().qhp_get_centroid(h, _dp(out)))
+    return out
+
+
+def qhp_get_beads(h) -> np.ndarray:
+    N, P = _dims(h)
+    out = np.empty((P, N, 3))
+    _check(lib().qhp_get_beads(h, _dp(out)))
+    return out
+
+
+def qhp_get_modes(h):
+    N, P = _dims(h)
+    Q, Pm = np.empty((N, 3, P)), np.empty((N, 3, P))
+    _check(lib().qhp_get_modes(h, _dp(Q), _dp(Pm)))
+    return Q, Pm
+
+
+def qhp_set_modes(h, Q, Pm) -> None:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    Pm = np.ascontiguousarray(Pm, dtype=np.float64)
+    _check(lib().qhp_set_modes(h, _dp(Q), _dp(Pm)))
+
+
+def qhp_set_modes_device(h, Q, Pm) -> None:
+    """Q, Pm: contiguous float64 CUDA tensors [N, 3, P] (or None)."""
+    _check(lib().qhp_set_modes_device(h, C.c_void_p(Q.data_ptr() if Q is not None else 0),
+                                      C.c_void_p(Pm.data_ptr() if Pm is not None else 0)))
+
+
+def qhp_get_modes_device(h, Q, Pm) -> None:
+    _check(lib().qhp_get_modes_device(h, C.c_void_p(Q.data_ptr() if Q is not None else 0),
+                                      C.c_void_p(Pm.data_ptr() if Pm is not None else 0)))
+
+
+def qhp_get_forces_device(h, out) -> None:
+    _check(lib().qhp_get_forces_device(h, C.c_void_p(out.data_ptr())))
+
+
+def qhp_get_state(h) -> bytes:
+    size = C.c_size_t(0)
+    _check(lib().qhp_get_state(h, None, C.byref(size)))
+    buf = C.create_string_buffer(size.value)
+    _check(lib().qhp_get_state(h, C.cast(buf, C.c_void_p), C.byref(size)))
+    return buf.raw
+
+
+def qhp_set_state(h, blob: bytes) -> None:
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib().qhp_set_state(h, C.cast(buf, C.c_void_p), len(blob)))
+
+
+def qhp_get_gamma(h, n_seg: int) -> np.ndarray:
+    out = np.empty((2, n_seg + 1))
+    _check(lib().qhp_get_gamma(h, _dp(out)))
+    return out
+
+
+def qhp_set_gamma(h, g) -> None:
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    _check(lib().qhp_set_gamma(h, _dp(g)))
+
+
+def qhp_get_qtb_noise(h, n_seg: int) -> np.ndarray:
+    N, _ = _dims(h)
+    out = np.empty((n_seg, 3 * N), dtype=np.float32)
+    _check(lib().qhp_get_qtb_noise(h, _fp(out)))
+    return out
+
+
+def qhp_get_qtb_records(h, n_seg: int):
+    N, _ = _dims(h)
+    v = np.empty((n_seg, 3 * N), dtype=np.float32)
+    F = np.empty((n_seg, 3 * N), dtype=np.float32)
+    _check(lib().qhp_get_qtb_records(h, _fp(v), _fp(F)))
+    return v, F
+
+
+def qhp_build_list(h) -> None:
+    _check(lib().qhp_build_list(h))
+
+
+def qhp_get_cells(h):
+    N, _ = _dims(h)
+    cell = np.empty(N, dtype=np.int32)
+    order = np.empty(N, dtype=np.int32)
+    _check(lib().qhp_get_cells(h, _ip(cell), _ip(order)))
+    return cell, order
+
+
+def qhp_get_list_pairs(h) -> np.ndarray:
+    cnt = C.c_int64(0)
+    _check(lib().qhp_get_list_pairs(h, None, 0, C.byref(cnt)))
+    out = np.empty((max(cnt.value, 1), 2), dtype=np.int64)
+    _check(lib().qhp_get_list_pairs(h, out.ctypes.data_as(C.POINTER(C.c_int64)), cnt.value, C.byref(cnt)))
+    return out[: cnt.value]
+
+
+def qhp_set_stream(h, stream_ptr: int | None) -> None:
+    _check(lib().qhp_set_stream(h, C.c_void_p(stream_ptr or 0)))
+
+
+def qhp_set_profiling(h, on: bool) -> None:
+    _check(lib().qhp_set_profiling(h, 1 if on else 0))
+
+
+def qhp_get_profile(h) -> qhp_profile:
+    p = qhp_profile()
+    _check(lib().qhp_get_profile(h, C.cast(C.byref(p), C.c_void_p)))
+    return p
+
+
+def qhp_count_pairs(h) -> tuple[int, int]:
+    a, b = C.c_int64(0), C.c_int64(0)
+    _check(lib().qhp_count_pairs(h, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+# ------------------------------------------------------------------ convenience
+
+def make_ff(rc: float, skin: float = 2.0, **kw) -> qhp_ff:
+    from .workloads import WATER_FF as W
+    p = dict(eps=W["eps"], sigma=W["sigma"], q_O=W["q_O"], k_b=W["k_b"], r0=W["r0"], k_theta=W["k_theta"],
+             theta0=math.radians(W["theta0_deg"]), alpha=W["alpha"], rc=rc, skin=skin, m_O=W["m_O"], m_H=W["m_H"])
+    p.update(kw)
+    return qhp_ff(**p)
+
+
+def make_thermo(kind: int = QHP_THERMO_PILE, gamma0: float = 1.0, dt_fs: float = 0.5, n_seg: int = 1024,
+                omega_cut_cm: float = 15000.0, a_gamma: float = 10.0, gamma_min_frac: float = 0.01,
+                adapt: int = QHP_ADAPT_SIMPLE, tau_ratio_ps: float = 1.0) -> qhp_thermo:
+    return qhp_thermo(kind, gamma0, dt_fs, n_seg, omega_cut_cm, a_gamma, gamma_min_frac, adapt, tau_ratio_ps)
+
+
+class System:
+    """Owns one qhp_sys handle (create, force field, beads, thermostat)."""
+
+    def __init__(self, box, types, molecule, pos, precision, ff: qhp_ff, P, temperature, seed,
+                 thermo: qhp_thermo | None = None):
+        self.h = qhp_create_system(types, molecule, pos, box, precision)
+        try:
+            qhp_set_forcefield(self.h, ff)
+            if thermo is not None and thermo.kind != QHP_THERMO_ADQTB:
+                qhp_set_thermostat(self.h, thermo)
+            qhp_set_beads(self.h, P, temperature, seed)
+            if thermo is not None and thermo.kind == QHP_THERMO_ADQTB:
+                qhp_set_thermostat(self.h, thermo)
+        except Exception:
+            qhp_destroy_system(self.h)
+            raise
+        self.n_atoms, self.P = len(types), P
+        self.thermo = thermo
+
+    @classmethod
+    def from_config(cls, cfg, precision=None, **over):
+        w = cfg.system()
+        prec = {"fp64": QHP_FP64, "mixed": QHP_MIXED}[precision or cfg.precision]
+        kind = QHP_THERMO_ADQTB if cfg.thermostat == "adqtb" else QHP_THERMO_PILE
+        th = make_thermo(kind=kind, gamma0=cfg.gamma0, dt_fs=cfg.dt_fs, n_seg=cfg.n_seg,
+                         omega_cut_cm=cfg.omega_cut_cm, a_gamma=cfg.a_gamma, gamma_min_frac=cfg.gamma_min_frac)
+        return cls(w.box, w.types, w.molecule, w.pos, prec, make_ff(cfg.rc, cfg.skin), cfg.P, cfg.temperature,
+                   over.get("seed", cfg.seed), th)
+
+    def close(self):
+        if self.h is not None:
+            qhp_destroy_system(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
