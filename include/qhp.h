@@ -190,6 +190,28 @@ int qhp_count_pairs(qhp_sys sys, int64_t* pairs, int64_t* oo_pairs);
  * library's own stream. */
 int qhp_set_stream(qhp_sys sys, void* stream);
 
+/* The spring, normal-mode kinetic and centroid-virial kinetic estimators of
+ * qhp_get_energy, computed on caller-owned device arrays without allocating any
+ * device memory.  The paper has no counterpart: this is a library convenience for
+ * callers that cannot allocate at the point of use (inside another framework's
+ * CUDA-graph capture, where cudaMalloc is not allowed; on threads that must not
+ * synchronise with the device; under an application-wide memory pool).
+ *   Q, Pm : device [n_atoms][3][P] modes (A) and momenta (amu A/ps), as qhp_get_modes_device;
+ *   F     : device [P][n_atoms][3] bead forces (kcal/mol/A), as qhp_get_forces_device,
+ *           or NULL (the virial term is then 0);
+ *   mass  : device [n_atoms] (amu);  out: device [3] = spring, kinetic_nm, kinetic_cv (kcal/mol);
+ *   stream: cudaStream_t (as void*), NULL for the legacy default stream.
+ * Work is enqueued asynchronously on the stream.  Partial sums live in one fixed
+ * device array of the library (1.5 MiB per GPU, held until the process exits):
+ * n_atoms may be at most 65536 * (64 / P), larger inputs return QHP_ERR_ARG.  The
+ * first call on a device looks up that array's address (cudaGetSymbolAddress), so
+ * make it before any stream capture.  Every call reuses the same array, overwriting
+ * it entirely (nothing needs clearing); calls that overlap on the GPU, e.g. on two
+ * streams at once, race on it and must be serialised by the caller.  P must be a
+ * power of two in [1, 64]. */
+int qhp_estimators_noalloc(int n_atoms, int P, double temperature, const double* Q, const double* Pm,
+                           const double* F, const double* mass, double* out, void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* qhp_last_error(void);
 

@@ -88,6 +88,7 @@ _SIGS = {
     "qhp_set_profiling": [_VP, C.c_int],
     "qhp_get_profile": [_VP, _VP],
     "qhp_count_pairs": [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "qhp_estimators_noalloc": [C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP],
 }
 
 
@@ -310,6 +311,14 @@ def qhp_get_profile(h) -> qhp_profile:
     p = qhp_profile()
     _check(lib().qhp_get_profile(h, C.cast(C.byref(p), C.c_void_p)))
     return p
+
+
+def qhp_estimators_noalloc(n_atoms: int, P: int, temperature: float, Q, Pm, F, mass, out, stream: int = 0) -> None:
+    """Device tensors in, device tensor out (see include/qhp.h); allocates nothing."""
+    def ptr(t):
+        return C.c_void_p(t.data_ptr() if t is not None else 0)
+    _check(lib().qhp_estimators_noalloc(int(n_atoms), int(P), float(temperature), ptr(Q), ptr(Pm), ptr(F), ptr(mass),
+                                        ptr(out), C.c_void_p(stream or 0)))
 
 
 def qhp_count_pairs(h) -> tuple[int, int]:
