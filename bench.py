@@ -64,7 +64,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -142,8 +142,9 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as td
         td.barrier()
     torch.cuda.synchronize(dev)
-    launches0 = qhp.qhp_get_info(h).kernel_launches
-    step_ms, pair_ms = [], []
+    info0 = qhp.qhp_get_info(h)
+    launches0, rebuilds0 = info0.kernel_launches, info0.rebuilds
+    step_ms, pair_ms, stages = [], [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -153,8 +154,12 @@ def run_ours(args, ws, rank, local):
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-            pair_ms.append(qhp.qhp_get_profile(h).pair_ms)
-    launches = qhp.qhp_get_info(h).kernel_launches - launches0
+            pr = qhp.qhp_get_profile(h)
+            pair_ms.append(pr.pair_ms)
+            stages.append([pr.integrate_ms, pr.list_ms, pr.pair_ms, pr.bonded_ms, pr.project_ms])
+    info1 = qhp.qhp_get_info(h)
+    launches = info1.kernel_launches - launches0
+    rebuilds = info1.rebuilds - rebuilds0
     total_ms = float(np.sum(step_ms))
     if dist:
         import torch.distributed as td
@@ -198,6 +203,9 @@ def run_ours(args, ws, rank, local):
                          "peak_source": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} clock)"},
             "clocks": clocks,
             "gpu_launches": int(launches),
+            "stage_ms": dict(zip(["integrate_transform", "list_check_rebuild", "pair", "bonded", "project_kick"],
+                                 [round(float(x), 5) for x in np.mean(np.array(stages), axis=0)])),
+            "list_rebuilds": int(rebuilds), "list_entries": int(info1.list_entries),
         }
     if args.e2e:
         e2e = _e2e(args, h, N, P, step, dev, ws)
@@ -349,7 +357,7 @@ def _profile_traffic(kind, workload):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rpmd_mixed_4096w")

@@ -441,6 +441,10 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
         set_error("temperature must be positive");
         return QHP_ERR_ARG;
     }
+    if ((int64_t)s->N * P >= (int64_t)1 << 30) {   // kernels use 32-bit (atom, bead) offsets
+        set_error("n_atoms * P must stay below 2^30");
+        return QHP_ERR_ARG;
+    }
     QHP_CUDA(cudaStreamSynchronize(s->stream));
     free_all(s);
     s->P = P;
@@ -453,7 +457,7 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     TRY(dalloc(s, &s->fmode, NP3));
     if (s->precision == QHP_MIXED) {
         TRY(dalloc(s, &s->Ffix, NP3));
-        TRY(dalloc(s, &s->pos_f, NP3));
+        TRY(dalloc(s, &s->pos_f4, (size_t)N * P));
         TRY(dalloc(s, &s->e_pair, (size_t)N * P));
         TRY(dalloc(s, &s->dA, (size_t)s->n_mol * 8));
     } else {
@@ -478,6 +482,7 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     TRY(dalloc(s, &s->cell_fill, ncell));
     TRY(dalloc(s, &s->cell_start, ncell + 1));
     TRY(dalloc(s, &s->cw, N));
+    TRY(dalloc(s, &s->cwl, N));
     TRY(dalloc(s, &s->nbr_start, N + 1));
     TRY(dalloc(s, &s->nbr_count, N));
     TRY(dalloc(s, &s->e_bond, (size_t)s->n_mol * P));

@@ -29,6 +29,8 @@ struct PairConsts {
     float rc2, rc, alpha, c2a, sc, ecut, sig2, eps4, eps24, ljshift, L, invL;
     double rc2_d, rc_d, alpha_d, c2a_d, sc_d, ecut_d, sig2_d, eps4_d, eps24_d, ljshift_d, L_d, invL_d, ke_d;
     float ke, qO_ke, qH_ke;
+    float p_alpha;        // A&S 7.1.26 p times alpha
+    float neg_a2_log2e;   // -alpha^2 log2(e)
 };
 
 // List entries carry the partner's sorted index in the low 31 bits and "partner is H"
@@ -37,23 +39,39 @@ constexpr int ENTRY_H_BIT = (int)0x80000000u;
 __device__ __forceinline__ int entry_j(int x) { return x & 0x7fffffff; }
 __device__ __forceinline__ bool entry_is_h(int x) { return x < 0; }
 
-// erfc(x) for x >= 0 with fractional error below 1.2e-7 everywhere: the Chebyshev fit
-// published in Numerical Recipes in C (2nd ed., Sec. 6.2, function erfcc),
-// erfc(x) = t exp(-x^2 + poly(t)), t = 1/(1 + x/2).  gauss receives exp(-x^2).
-__device__ __forceinline__ float erfc_cheb(float x, float& gauss) {
-    const float t = __fdividef(1.0f, fmaf(0.5f, x, 1.0f));
-    float p = 0.17087277f;
-    p = fmaf(p, t, -0.82215223f);
-    p = fmaf(p, t, 1.48851587f);
-    p = fmaf(p, t, -1.13520398f);
-    p = fmaf(p, t, 0.27886807f);
-    p = fmaf(p, t, -0.18628806f);
-    p = fmaf(p, t, 0.09678418f);
-    p = fmaf(p, t, 0.37409196f);
-    p = fmaf(p, t, 1.00002368f);
-    p = fmaf(p, t, -1.26551223f);
-    gauss = __expf(-x * x);
-    return t * gauss * __expf(p);
+// Hardware approximations of the special-function unit, flush-to-zero (pair distances
+// are never denormal): reciprocal square root (rel. error < 2^-22.9), reciprocal and
+// base-2 exponential (a few ulp), written as PTX so that no range fix-up code surrounds them.
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_fast(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// erfc(a r) for a r >= 0 with absolute error below 1.5e-7: the rational approximation
+// 7.1.26 of Abramowitz & Stegun (Handbook of Mathematical Functions, 1964; from Hastings),
+// erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1/(1 + p x).
+// The factor exp(-a^2 r^2) is the Gaussian the DSF force needs anyway: it is formed from
+// r^2 directly (exponent -a^2 log2(e) r^2 for the base-2 exponential); gauss receives it.
+__device__ __forceinline__ float erfc_as(float r, float r2, const PairConsts& c, float& gauss) {
+    const float t = rcp_fast(fmaf(c.p_alpha, r, 1.0f));
+    float p = 1.061405429f;
+    p = fmaf(p, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    gauss = ex2_fast(c.neg_a2_log2e * r2);
+    return t * p * gauss;
 }
 
 // One bead pair: DSF Coulomb (+ shifted LJ on O-O), force on i accumulated as -g d.
@@ -67,10 +85,10 @@ __device__ __forceinline__ void pair_term(float dx, float dy, float dz, float qq
     }
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 < c.rc2) {
-        const float rinv = rsqrtf(r2);
+        const float rinv = rsqrt_fast(r2);
         const float r = r2 * rinv;
         float gauss;
-        const float erfc_ar = erfc_cheb(c.alpha * r, gauss);
+        const float erfc_ar = erfc_as(r, r2, c, gauss);
         const float rinv2 = rinv * rinv;
         // -V'(r)/r = qq (erfc(a r)/r^2 + (2a/sqrt(pi)) e^{-a^2 r^2}/r - S_c) / r
         float g = qq * fmaf(erfc_ar, rinv2, fmaf(c.c2a * gauss, rinv, -c.sc)) * rinv;
@@ -89,68 +107,71 @@ __device__ __forceinline__ void pair_term(float dx, float dy, float dz, float qq
     }
 }
 
+constexpr int PAIR_WARPS = 4;
+
 template <int P, bool ALL, bool ENERGY>
-__global__ void __launch_bounds__(128) k_pair_mixed(int N, const float* __restrict__ pos, const int* __restrict__ start,
+__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const float4* __restrict__ pos, const int* __restrict__ start,
                                                     const int4* __restrict__ nbr, const float* __restrict__ charge_s,
                                                     const int* __restrict__ type_s, const int* __restrict__ perm,
                                                     long long* __restrict__ F, float* __restrict__ epair, PairConsts c,
                                                     const unsigned* __restrict__ status) {
     constexpr int JPW = P >= 32 ? 1 : 32 / P;
     constexpr int BPL = P > 32 ? P / 32 : 1;
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= N) return;
+    constexpr int NB = P > 32 ? P : 32;                   // bead slots reduced across warps
+    __shared__ float red[PAIR_WARPS][4][NB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x;                             // one atom per block, PAIR_WARPS warps on its list
     const int b0 = P >= 32 ? lane : (lane % P);
     const int jsub = P >= 32 ? 0 : lane / P;
     const bool ok = (*status & ST_LIST_OVERFLOW) == 0u;
-    const float* __restrict__ px = pos;
-    const float* __restrict__ py = pos + (size_t)N * P;
-    const float* __restrict__ pz = pos + (size_t)2 * N * P;
+    // N * P < 2^30 is checked at set-up, so 32-bit element offsets suffice
+    const float4* __restrict__ pl = pos + b0;
 
     float xi[BPL], yi[BPL], zi[BPL], fx[BPL], fy[BPL], fz[BPL], en[BPL];
 #pragma unroll
     for (int u = 0; u < BPL; ++u) {
-        const size_t o = (size_t)i * P + b0 + 32 * u;
-        xi[u] = px[o];
-        yi[u] = py[o];
-        zi[u] = pz[o];
+        const float4 p = pl[i * P + 32 * u];
+        xi[u] = p.x;
+        yi[u] = p.y;
+        zi[u] = p.z;
         fx[u] = fy[u] = fz[u] = en[u] = 0.0f;
     }
     const float qi = charge_s[i];
     const bool Oi = type_s[i] == 0;
     const float qO = qi * c.qO_ke, qH = qi * c.qH_ke;
-    const int k1 = ok ? start[i + 1] : start[i];
-    int k = start[i] + jsub;
+    // the list of i is cut into PAIR_WARPS contiguous chunks, one per warp
+    const int ka = start[i], kb = ok ? start[i + 1] : start[i];
+    const int chunk = ((kb - ka + PAIR_WARPS - 1) / PAIR_WARPS + JPW - 1) / JPW * JPW;
+    const int kw0 = min(kb, ka + w * chunk), k1 = min(kb, kw0 + chunk);
+    int k = kw0 + jsub;
     // two list entries per iteration: both entries and all their loads are in flight together
     for (; k + JPW < k1; k += 2 * JPW) {
         const int4 e0 = __ldg(&nbr[k]);
         const int4 e1 = __ldg(&nbr[k + JPW]);
-        const int j0 = entry_j(e0.x), j1 = entry_j(e1.x);
+        const int j0 = entry_j(e0.x) * P, j1 = entry_j(e1.x) * P;
         const bool h0 = entry_is_h(e0.x), h1 = entry_is_h(e1.x);
 #pragma unroll
         for (int u = 0; u < BPL; ++u) {
-            const size_t o0 = (size_t)j0 * P + b0 + 32 * u, o1 = (size_t)j1 * P + b0 + 32 * u;
-            const float ax = __ldg(&px[o0]), ay = __ldg(&py[o0]), az = __ldg(&pz[o0]);
-            const float bx = __ldg(&px[o1]), by = __ldg(&py[o1]), bz = __ldg(&pz[o1]);
-            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (ax - xi[u]), __int_as_float(e0.z) + (ay - yi[u]),
-                                   __int_as_float(e0.w) + (az - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u], fy[u],
+            const float4 a = __ldg(&pl[j0 + 32 * u]);
+            const float4 b = __ldg(&pl[j1 + 32 * u]);
+            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
+                                   __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u], fy[u],
                                    fz[u], en[u]);
-            pair_term<ALL, ENERGY>(__int_as_float(e1.y) + (bx - xi[u]), __int_as_float(e1.z) + (by - yi[u]),
-                                   __int_as_float(e1.w) + (bz - zi[u]), h1 ? qH : qO, Oi && !h1, c, fx[u], fy[u],
+            pair_term<ALL, ENERGY>(__int_as_float(e1.y) + (b.x - xi[u]), __int_as_float(e1.z) + (b.y - yi[u]),
+                                   __int_as_float(e1.w) + (b.z - zi[u]), h1 ? qH : qO, Oi && !h1, c, fx[u], fy[u],
                                    fz[u], en[u]);
         }
     }
     if (k < k1) {
         const int4 e0 = __ldg(&nbr[k]);
-        const int j0 = entry_j(e0.x);
+        const int j0 = entry_j(e0.x) * P;
         const bool h0 = entry_is_h(e0.x);
 #pragma unroll
         for (int u = 0; u < BPL; ++u) {
-            const size_t o0 = (size_t)j0 * P + b0 + 32 * u;
-            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (__ldg(&px[o0]) - xi[u]),
-                                   __int_as_float(e0.z) + (__ldg(&py[o0]) - yi[u]),
-                                   __int_as_float(e0.w) + (__ldg(&pz[o0]) - zi[u]), h0 ? qH : qO, Oi && !h0, c,
-                                   fx[u], fy[u], fz[u], en[u]);
+            const float4 a = __ldg(&pl[j0 + 32 * u]);
+            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
+                                   __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u], fy[u],
+                                   fz[u], en[u]);
         }
     }
     if (P < 32) {
@@ -163,14 +184,34 @@ __global__ void __launch_bounds__(128) k_pair_mixed(int N, const float* __restri
         }
     }
     if (jsub == 0) {
+#pragma unroll
+        for (int u = 0; u < BPL; ++u) {
+            const int b = b0 + 32 * u;
+            red[w][0][b] = fx[u];
+            red[w][1][b] = fy[u];
+            red[w][2][b] = fz[u];
+            red[w][3][b] = en[u];
+        }
+    }
+    __syncthreads();
+    // warp 0 adds the chunks in a fixed order and writes each bead force once
+    if (w == 0 && jsub == 0) {
         const int a = perm[i];
 #pragma unroll
         for (int u = 0; u < BPL; ++u) {
             const int b = b0 + 32 * u;
-            F[((size_t)a * 3 + 0) * P + b] = __float2ll_rn(fx[u] * FIX_SCALE_F);
-            F[((size_t)a * 3 + 1) * P + b] = __float2ll_rn(fy[u] * FIX_SCALE_F);
-            F[((size_t)a * 3 + 2) * P + b] = __float2ll_rn(fz[u] * FIX_SCALE_F);
-            if (ENERGY) epair[(size_t)i * P + b] = en[u];
+            float sx = red[0][0][b], sy = red[0][1][b], sz = red[0][2][b], se = red[0][3][b];
+#pragma unroll
+            for (int v = 1; v < PAIR_WARPS; ++v) {
+                sx += red[v][0][b];
+                sy += red[v][1][b];
+                sz += red[v][2][b];
+                se += red[v][3][b];
+            }
+            F[((size_t)a * 3 + 0) * P + b] = __float2ll_rn(sx * FIX_SCALE_F);
+            F[((size_t)a * 3 + 1) * P + b] = __float2ll_rn(sy * FIX_SCALE_F);
+            F[((size_t)a * 3 + 2) * P + b] = __float2ll_rn(sz * FIX_SCALE_F);
+            if (ENERGY) epair[(size_t)i * P + b] = se;
         }
     }
 }
@@ -257,7 +298,7 @@ struct BondConsts {
 
 // Bonded terms per (molecule, bead); each thread owns the forces of its three atoms at its bead.
 template <bool MIXED, bool ENERGY>
-__global__ void k_bonded(int n_mol, int N, int P, const float* __restrict__ pos_f, const double* __restrict__ pos_d,
+__global__ void k_bonded(int n_mol, int N, int P, const float4* __restrict__ pos_f, const double* __restrict__ pos_d,
                          const float* __restrict__ dA, const int* __restrict__ iperm, long long* Ffix, double* Fd,
                          double* ebond, BondConsts c) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -267,11 +308,15 @@ __global__ void k_bonded(int n_mol, int N, int P, const float* __restrict__ pos_
     const int sO = iperm[aO], s1 = iperm[aH1], s2 = iperm[aH2];
     if (MIXED) {
         float d1[3], d2[3];
-        for (int d = 0; d < 3; ++d) {
-            const float xo = pos_f[((size_t)d * N + sO) * P + b];
-            d1[d] = (pos_f[((size_t)d * N + s1) * P + b] - xo) + dA[((size_t)m * 2 + 0) * 4 + d];
-            d2[d] = (pos_f[((size_t)d * N + s2) * P + b] - xo) + dA[((size_t)m * 2 + 1) * 4 + d];
-        }
+        const float4 xo = pos_f[(size_t)sO * P + b], x1 = pos_f[(size_t)s1 * P + b], x2 = pos_f[(size_t)s2 * P + b];
+        const float4 a1 = reinterpret_cast<const float4*>(dA)[(size_t)m * 2 + 0];
+        const float4 a2 = reinterpret_cast<const float4*>(dA)[(size_t)m * 2 + 1];
+        d1[0] = (x1.x - xo.x) + a1.x;
+        d1[1] = (x1.y - xo.y) + a1.y;
+        d1[2] = (x1.z - xo.z) + a1.z;
+        d2[0] = (x2.x - xo.x) + a2.x;
+        d2[1] = (x2.y - xo.y) + a2.y;
+        d2[2] = (x2.z - xo.z) + a2.z;
         const float r1 = sqrtf(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
         const float r2 = sqrtf(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
         float cs = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
@@ -325,7 +370,7 @@ __global__ void k_bonded(int n_mol, int N, int P, const float* __restrict__ pos_
 }
 
 // Count in-cutoff bead pairs j > i (lane = bead, one list entry at a time); not on the step path.
-__global__ void k_count_pairs(int N, int P, int mixed, int all, const float* __restrict__ pos_f,
+__global__ void k_count_pairs(int N, int P, int mixed, int all, const float4* __restrict__ pos_f,
                               const double* __restrict__ pos_d, const int* __restrict__ start,
                               const int4* __restrict__ nbr, const int* __restrict__ type_s, PairConsts c,
                               unsigned long long* out2) {
@@ -340,9 +385,10 @@ __global__ void k_count_pairs(int N, int P, int mixed, int all, const float* __r
             if (j <= i) continue;
             double r2;
             if (mixed) {
-                float dx = __int_as_float(e.y) + (pos_f[((size_t)0 * N + j) * P + b] - pos_f[((size_t)0 * N + i) * P + b]);
-                float dy = __int_as_float(e.z) + (pos_f[((size_t)1 * N + j) * P + b] - pos_f[((size_t)1 * N + i) * P + b]);
-                float dz = __int_as_float(e.w) + (pos_f[((size_t)2 * N + j) * P + b] - pos_f[((size_t)2 * N + i) * P + b]);
+                const float4 pj = pos_f[(size_t)j * P + b], pi = pos_f[(size_t)i * P + b];
+                float dx = __int_as_float(e.y) + (pj.x - pi.x);
+                float dy = __int_as_float(e.z) + (pj.y - pi.y);
+                float dz = __int_as_float(e.w) + (pj.z - pi.z);
                 if (all) {
                     dx -= c.L * rintf(dx * c.invL);
                     dy -= c.L * rintf(dy * c.invL);
@@ -403,6 +449,8 @@ PairConsts make_pair_consts(const qhp_system_s* s) {
     c.ke = (float)COULOMB;
     c.qO_ke = (float)(COULOMB * f.q_O);
     c.qH_ke = (float)(COULOMB * (-0.5 * f.q_O));
+    c.p_alpha = (float)(0.3275911 * a);
+    c.neg_a2_log2e = (float)(-a * a * 1.4426950408889634);
     return c;
 }
 
@@ -410,20 +458,20 @@ template <int P>
 void pair_mixed_dispatch(qhp_system_s* s, bool energy, const PairConsts& c, int grid) {
     if (s->list_mode) {
         if (energy)
-            k_pair_mixed<P, false, true><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr, s->charge_s,
+            k_pair_mixed<P, false, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr, s->charge_s,
                                                                       s->type_s, s->perm, s->Ffix, s->e_pair, c,
                                                                       s->status);
         else
-            k_pair_mixed<P, false, false><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr,
+            k_pair_mixed<P, false, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr,
                                                                        s->charge_s, s->type_s, s->perm, s->Ffix,
                                                                        s->e_pair, c, s->status);
     } else {
         if (energy)
-            k_pair_mixed<P, true, true><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr, s->charge_s,
+            k_pair_mixed<P, true, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr, s->charge_s,
                                                                      s->type_s, s->perm, s->Ffix, s->e_pair, c,
                                                                      s->status);
         else
-            k_pair_mixed<P, true, false><<<grid, 128, 0, s->stream>>>(s->N, s->pos_f, s->nbr_start, s->nbr,
+            k_pair_mixed<P, true, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr,
                                                                       s->charge_s, s->type_s, s->perm, s->Ffix,
                                                                       s->e_pair, c, s->status);
     }
@@ -434,15 +482,16 @@ void pair_mixed_dispatch(qhp_system_s* s, bool energy, const PairConsts& c, int 
 cudaError_t launch_pair(qhp_system_s* s, bool energy) {
     const PairConsts c = make_pair_consts(s);
     const int grid = (s->N * 32 + 127) / 128;
+    const int gm = s->N;   // mixed: one block per sorted atom
     if (s->precision == QHP_MIXED) {
         switch (s->P) {
-            case 1: pair_mixed_dispatch<1>(s, energy, c, grid); break;
-            case 2: pair_mixed_dispatch<2>(s, energy, c, grid); break;
-            case 4: pair_mixed_dispatch<4>(s, energy, c, grid); break;
-            case 8: pair_mixed_dispatch<8>(s, energy, c, grid); break;
-            case 16: pair_mixed_dispatch<16>(s, energy, c, grid); break;
-            case 32: pair_mixed_dispatch<32>(s, energy, c, grid); break;
-            case 64: pair_mixed_dispatch<64>(s, energy, c, grid); break;
+            case 1: pair_mixed_dispatch<1>(s, energy, c, gm); break;
+            case 2: pair_mixed_dispatch<2>(s, energy, c, gm); break;
+            case 4: pair_mixed_dispatch<4>(s, energy, c, gm); break;
+            case 8: pair_mixed_dispatch<8>(s, energy, c, gm); break;
+            case 16: pair_mixed_dispatch<16>(s, energy, c, gm); break;
+            case 32: pair_mixed_dispatch<32>(s, energy, c, gm); break;
+            case 64: pair_mixed_dispatch<64>(s, energy, c, gm); break;
             default: return cudaErrorInvalidValue;
         }
     } else {
@@ -465,11 +514,11 @@ cudaError_t launch_bonded(qhp_system_s* s, bool energy) {
     const int g2 = (nt + 127) / 128;
     const bool mixed = s->precision == QHP_MIXED;
     if (mixed) {
-        if (energy) k_bonded<true, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
-        else k_bonded<true, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+        if (energy) k_bonded<true, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+        else k_bonded<true, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
     } else {
-        if (energy) k_bonded<false, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
-        else k_bonded<false, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+        if (energy) k_bonded<false, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+        else k_bonded<false, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
     }
     s->launches += 1;
     return cudaGetLastError();
@@ -489,7 +538,7 @@ cudaError_t launch_forces(qhp_system_s* s, bool energy) {
 cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2) {
     const PairConsts c = make_pair_consts(s);
     const int grid = (s->N * 32 + 127) / 128;
-    k_count_pairs<<<grid, 128, 0, s->stream>>>(s->N, s->P, s->precision == QHP_MIXED, s->list_mode, s->pos_f, s->pos_d,
+    k_count_pairs<<<grid, 128, 0, s->stream>>>(s->N, s->P, s->precision == QHP_MIXED, s->list_mode, s->pos_f4, s->pos_d,
                                                s->nbr_start, s->nbr, s->type_s, c, out2);
     s->launches += 1;
     return cudaGetLastError();

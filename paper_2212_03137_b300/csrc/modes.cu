@@ -28,7 +28,7 @@ struct IntegrateArgs {
     const int* iperm;
     const double* Tm;      // sqrt(P) T[b][n]
     const float* Tmf;
-    float* pos_f;
+    float4* pos_f4;
     double* pos_d;
     unsigned* dev_max;
     const float* qtb_u;
@@ -129,9 +129,7 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(IntegrateArgs A) {
             // below the pair arithmetic's own rounding.
             float acc = 0.0f;
             for (int k = 1; k < P; ++k) acc = fmaf(Tsf[k * P + n], qf[base + k], acc);
-            const float x = (float)(qs[base] - anc) + acc;
-            A.pos_f[((size_t)d * A.N + s) * P + n] = x;
-            xr[t] = x;
+            xr[t] = (float)(qs[base] - anc) + acc;
         } else {
             double acc = 0.0;
             for (int k = 0; k < P; ++k) acc = fma(Tsd[k * P + n], qs[base + k], acc);
@@ -144,6 +142,8 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(IntegrateArgs A) {
         const int base = la * 3 * P;
         const float x0 = xr[base + n], x1 = xr[base + P + n], x2 = xr[base + 2 * P + n];
         dv = x0 * x0 + x1 * x1 + x2 * x2;
+        // mixed: one 16-byte (x, y, z, 0) record per (sorted atom, bead) for the pair kernel
+        if (MIXED) A.pos_f4[(size_t)A.iperm[a] * P + n] = make_float4(x0, x1, x2, 0.0f);
     }
     block_max_atomic(dv, A.dev_max);
 }
@@ -355,7 +355,7 @@ static IntegrateArgs make_iargs(qhp_system_s* s) {
     A.iperm = s->iperm;
     A.Tm = s->Tmat;
     A.Tmf = s->Tmat_f;
-    A.pos_f = s->pos_f;
+    A.pos_f4 = s->pos_f4;
     A.pos_d = s->pos_d;
     A.dev_max = s->dev_max;
     A.qtb_u = s->qtb_u;

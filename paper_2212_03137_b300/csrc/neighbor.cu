@@ -22,6 +22,31 @@ __device__ __forceinline__ double min_image_rn(double d, double L) {
     return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
 }
 
+// Error-free transformation a + b = s + e (Knuth's TwoSum; additions only, so no FMA
+// contraction can alter it).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hj + lj) + (sh + sl) - (hi + li), the result small while the terms are up to a box
+// length: the large parts are combined exactly, so the FP32 result is essentially the
+// correctly rounded separation.
+__device__ __forceinline__ float sep_df(float hj, float lj, float hi, float li, float sh, float sl) {
+    float s1, e1, s2, e2;
+    two_sum(hj, sh, s1, e1);
+    two_sum(s1, -hi, s2, e2);
+    return s2 + ((e1 + e2) + ((lj - li) + sl));
+}
+
+// Same image for |d| < L/2 - tiny, by a multiply instead of a correctly rounded divide;
+// used for the anchor separations stored in list entries, which need accuracy, not bit
+// equality with the list definition (FP64 division is expensive on this part).
+__device__ __forceinline__ double min_image_fast(double d, double L, double invL) {
+    return fma(-L, rint(d * invL), d);
+}
+
 __device__ __forceinline__ int cell_coord(double C, double L, int n_c, double* frac_out) {
     const double t = __ddiv_rn(C, L);
     double frac = __dsub_rn(t, floor(t));
@@ -145,7 +170,7 @@ __global__ void k_identity_order(const int* flag, int N, int* perm, int* iperm) 
 // Sorted per-atom attributes, FP32 wrapped centroids and (mixed) intramolecular anchor offsets.
 __global__ void k_sorted_attrs(const int* flag, int N, double L, const int* perm, const int* type, const int* mol,
                                const double* anchor, float q_O, float q_H, float* charge_s, int* type_s, int* mol_s,
-                               float4* cw, float* dA) {
+                               float4* cw, float4* cwl, float* dA) {
     if (!*flag) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
@@ -160,7 +185,9 @@ __global__ void k_sorted_attrs(const int* flag, int N, double L, const int* perm
         (void)cell_coord(anchor[a * 3 + d], L, 1, &fr);
         w[d] = fr * L;
     }
-    cw[s] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.0f);
+    const float h0 = (float)w[0], h1 = (float)w[1], h2 = (float)w[2];
+    cw[s] = make_float4(h0, h1, h2, 0.0f);
+    cwl[s] = make_float4((float)(w[0] - (double)h0), (float)(w[1] - (double)h1), (float)(w[2] - (double)h2), 0.0f);
     if (dA && (a % 3) != 0) {     // H atom: min-image A_H - A_O of its molecule
         const int o = a - (a % 3);
         float* out = dA + ((size_t)(a / 3) * 2 + (a % 3) - 1) * 4;
@@ -172,8 +199,9 @@ __global__ void k_sorted_attrs(const int* flag, int N, double L, const int* perm
 // Centroid Verlet list, warp per sorted atom i; FILL = false counts, true writes entries.
 template <bool FILL>
 __global__ void k_list(const int* flag, int N, double L, int n_c, double r2max, float lo2, float hi2,
-                       const int* perm, const int* cell, const int* cell_start, const float4* cw, const int* mol_s,
-                       const int* type_s, const double* anchor, int* count, const int* start, int4* nbr, int64_t cap) {
+                       const int* perm, const int* cell, const int* cell_start, const float4* cw, const float4* cwl,
+                       const int* mol_s, const int* type_s, const double* anchor, int* count, const int* start,
+                       int4* nbr, int64_t cap) {
     if (!*flag) return;
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -182,6 +210,8 @@ __global__ void k_list(const int* flag, int N, double L, int n_c, double r2max, 
     const int ci = cell[ai];
     const int cx = ci % n_c, cy = (ci / n_c) % n_c, cz = ci / (n_c * n_c);
     const float4 wi = cw[i];
+    const float4 li = FILL ? cwl[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float Llo = (float)(L - (double)(float)L);   // L = Lf + Llo
     const int mi = mol_s[i];
     const double Ci0 = anchor[ai * 3], Ci1 = anchor[ai * 3 + 1], Ci2 = anchor[ai * 3 + 2];
     const float Lf = (float)L;
@@ -219,10 +249,11 @@ __global__ void k_list(const int* flag, int N, double L, int n_c, double r2max, 
                     if (FILL && acc) {
                         const int64_t pos = (int64_t)base + cnt + __popc(bal & ((1u << lane) - 1u));
                         if (pos < cap) {
-                            const int aj = perm[j];
-                            const float Dx = (float)min_image_rn(anchor[aj * 3] - Ci0, L);
-                            const float Dy = (float)min_image_rn(anchor[aj * 3 + 1] - Ci1, L);
-                            const float Dz = (float)min_image_rn(anchor[aj * 3 + 2] - Ci2, L);
+                            // D_ij = (w_j + stencil shift) - w_i from the double-float wrapped anchors
+                            const float4 wj = cw[j], lj = cwl[j];
+                            const float Dx = sep_df(wj.x, lj.x, wi.x, li.x, sx, sx > 0.f ? Llo : (sx < 0.f ? -Llo : 0.f));
+                            const float Dy = sep_df(wj.y, lj.y, wi.y, li.y, sy, sy > 0.f ? Llo : (sy < 0.f ? -Llo : 0.f));
+                            const float Dz = sep_df(wj.z, lj.z, wi.z, li.z, sz, sz > 0.f ? Llo : (sz < 0.f ? -Llo : 0.f));
                             nbr[pos] = make_int4(j | (type_s[j] ? (int)0x80000000u : 0), __float_as_int(Dx),
                                                  __float_as_int(Dy), __float_as_int(Dz));
                         }
@@ -251,9 +282,10 @@ __global__ void k_list_all(const int* flag, int N, double L, const int* mol_s, c
         if (FILL && acc) {
             const int64_t pos = (int64_t)base + cnt + __popc(bal & ((1u << lane) - 1u));
             if (pos < cap) {
-                const float Dx = (float)min_image_rn(anchor[j * 3] - anchor[i * 3], L);
-                const float Dy = (float)min_image_rn(anchor[j * 3 + 1] - anchor[i * 3 + 1], L);
-                const float Dz = (float)min_image_rn(anchor[j * 3 + 2] - anchor[i * 3 + 2], L);
+                const double iL = 1.0 / L;
+                const float Dx = (float)min_image_fast(anchor[j * 3] - anchor[i * 3], L, iL);
+                const float Dy = (float)min_image_fast(anchor[j * 3 + 1] - anchor[i * 3 + 1], L, iL);
+                const float Dz = (float)min_image_fast(anchor[j * 3 + 2] - anchor[i * 3 + 2], L, iL);
                 nbr[pos] = make_int4(j | (type_s[j] ? (int)0x80000000u : 0), __float_as_int(Dx), __float_as_int(Dy),
                                      __float_as_int(Dz));
             }
@@ -294,21 +326,21 @@ cudaError_t launch_rebuild(qhp_system_s* s) {
         s->launches += 2;
     }
     k_sorted_attrs<<<gN, tb, 0, st>>>(flag, N, s->L, s->perm, s->type_d, s->mol_d, s->anchor, (float)s->ff.q_O,
-                                      (float)(-0.5 * s->ff.q_O), s->charge_s, s->type_s, s->mol_s, s->cw,
+                                      (float)(-0.5 * s->ff.q_O), s->charge_s, s->type_s, s->mol_s, s->cw, s->cwl,
                                       s->precision == QHP_MIXED ? s->dA : nullptr);
     const int wb = 128, gW = (N * 32 + wb - 1) / wb;
     const double r2max = s->r_list * s->r_list;
     const float lo = (float)(s->r_list - 1e-3), hi = (float)(s->r_list + 1e-3);
     if (s->list_mode) {
         k_list<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
-                                         s->cell_start, s->cw, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+                                         s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
     } else {
         k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
     }
     k_scan<<<1, 1024, 0, st>>>(flag, s->nbr_count, s->nbr_start, N, s->nbr_cap, s->nbr_total, s->status);
     if (s->list_mode) {
         k_list<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
-                                        s->cell_start, s->cw, s->mol_s, s->type_s, s->anchor, nullptr, s->nbr_start, s->nbr,
+                                        s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor, nullptr, s->nbr_start, s->nbr,
                                         s->nbr_cap);
     } else {
         k_list_all<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, nullptr, s->nbr_start, s->nbr,
@@ -340,14 +372,14 @@ int host_list_size(qhp_system_s* s, int64_t* total) {
         k_identity_order<<<gN, tb, 0, st>>>(flag, N, s->perm, s->iperm);
     }
     k_sorted_attrs<<<gN, tb, 0, st>>>(flag, N, s->L, s->perm, s->type_d, s->mol_d, s->anchor, (float)s->ff.q_O,
-                                      (float)(-0.5 * s->ff.q_O), s->charge_s, s->type_s, s->mol_s, s->cw,
+                                      (float)(-0.5 * s->ff.q_O), s->charge_s, s->type_s, s->mol_s, s->cw, s->cwl,
                                       s->precision == QHP_MIXED ? s->dA : nullptr);
     const int wb = 128, gW = (N * 32 + wb - 1) / wb;
     const double r2max = s->r_list * s->r_list;
     const float lo = (float)(s->r_list - 1e-3), hi = (float)(s->r_list + 1e-3);
     if (s->list_mode)
         k_list<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
-                                         s->cell_start, s->cw, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+                                         s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
     else
         k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
     k_scan<<<1, 1024, 0, st>>>(flag, s->nbr_count, s->nbr_start, N, -1, s->nbr_total, s->status);

@@ -137,7 +137,7 @@ struct qhp_system_s {
     double *Q = nullptr, *Pm = nullptr, *fmode = nullptr;    // [N][3][P]
     double *Fd = nullptr;                                    // FP64 bead forces [N][3][P]
     long long* Ffix = nullptr;                               // mixed bead forces, fixed point [N][3][P]
-    float* pos_f = nullptr;                                  // mixed: sorted [3][N][P], x - anchor
+    float4* pos_f4 = nullptr;                                // mixed: sorted [N][P] (x, y, z, 0) - anchor
     double* pos_d = nullptr;                                 // fp64: sorted [3][N][P], absolute
     double* anchor = nullptr;                                // [N][3] centroids at the last build
     float* dA = nullptr;                                     // mixed: [n_mol][2][4] min-image A_H - A_O
@@ -151,6 +151,7 @@ struct qhp_system_s {
     int *perm = nullptr, *iperm = nullptr;                   // sorted -> atom, atom -> sorted
     int *cell = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr, *tmp_idx = nullptr;
     float4* cw = nullptr;                                    // sorted wrapped centroids (FP32) for the prefilter
+    float4* cwl = nullptr;                                   // their low parts: wrapped = cw + cwl (double-float)
     int* nbr_start = nullptr;                                // [N+1]
     int* nbr_count = nullptr;                                // [N]
     int4* nbr = nullptr;                                     // entries {j, Dx, Dy, Dz}
