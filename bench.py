@@ -302,6 +302,7 @@ def _cpu_baseline(cfg, args, n_beads=2):
     """cpu_baseline leg: the oracle timed on the host cores, and the GPU force error on the
     same sampled beads at the same initial state."""
     from paper_2212_03137_b300 import qhp
+    n_beads = min(n_beads, cfg.P)
     t, units, xb, F, t_force, t_int = _oracle_sample(cfg, n_beads)
     err = None
     s = qhp.System.from_config(cfg)

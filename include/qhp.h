@@ -170,6 +170,9 @@ int qhp_get_qtb_records(qhp_sys sys, float* v, float* F);
 int qhp_build_list(qhp_sys sys);
 int qhp_get_cells(qhp_sys sys, int* cell, int* order);
 int qhp_get_list_pairs(qhp_sys sys, int64_t* pairs, int64_t cap, int64_t* count);
+/* The list row of one atom: partner atom indices (in list order, at most cap of them);
+ * *count receives the row length. */
+int qhp_get_list_row(qhp_sys sys, int atom, int* partners, int cap, int* count);
 
 int qhp_get_info(qhp_sys sys, qhp_info* out);
 

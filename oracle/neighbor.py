@@ -6,7 +6,8 @@ so one list serves all P beads.  The paper does not define the cells or the
 list radius; the readings used here are:
 
 * list radius r_list = rc + skin;
-* cell grid n_c = floor(L / r_list) per dimension (cells at least r_list wide);
+* cell grid n_c = floor(2 L / r_list) per dimension (cells at least r_list / 2 wide, so
+  every partner of an atom lies within two cells of it: a 5 x 5 x 5 stencil);
 * cell of a centroid C: t = C/L, frac = t - floor(t) (set to 0 when it rounds
   to 1), cell index per dimension min(floor(frac * n_c), n_c - 1), linear id
   (cz * n_c + cy) * n_c + cx;
@@ -27,7 +28,7 @@ import numpy as np
 
 
 def cell_grid(L: float, r_list: float) -> int:
-    return int(math.floor(L / r_list))
+    return int(math.floor(2.0 * L / r_list))
 
 
 def assign_cells(C: np.ndarray, L: float, n_c: int) -> np.ndarray:
@@ -77,7 +78,7 @@ def neighbours_of(i: int, C: np.ndarray, mol: np.ndarray, L: float, r_list: floa
 
 def use_centroid_list(L: float, rc: float, skin: float) -> bool:
     """Reading for small boxes: the centroid list is used only when the cell grid is at
-    least 3 wide (27 distinct neighbour cells) and r_list < L/2; otherwise every pair of
+    least 5 wide (125 distinct stencil cells) and r_list < L/2; otherwise every pair of
     different molecules is visited with a per-bead minimum image."""
     r_list = rc + skin
-    return cell_grid(L, r_list) >= 3 and r_list < 0.5 * L
+    return cell_grid(L, r_list) >= 5 and r_list < 0.5 * L

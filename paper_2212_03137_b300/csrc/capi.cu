@@ -96,7 +96,7 @@ __global__ void k_sum_final(const double* part, int n, double* out) {
 
 int check_status(qhp_system_s* s, unsigned st) {
     if (st & ST_LIST_OVERFLOW) {
-        qhp::set_error("neighbour list overflow (entries exceed the buffer of %lld)", (long long)s->nbr_cap);
+        qhp::set_error("neighbour list overflow (a row exceeds its %d entries)", s->row_cap);
         return QHP_ERR_LIST_OVERFLOW;
     }
     if (st & ST_NONFINITE) {
@@ -156,6 +156,80 @@ int enqueue_forces(qhp_system_s* s, bool force_rebuild, bool energy) {
     return QHP_OK;
 }
 
+// While a step graph is being captured: add an IF node driven by k_check and capture the
+// list rebuild chain (cells, sort, list, positions) into its body on the auxiliary stream,
+// so steps without a rebuild launch none of those kernels.
+int enqueue_rebuild_conditional(qhp_system_s* s) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    QHP_CUDA(cudaStreamGetCaptureInfo(s->stream, &st, nullptr, &cg, &deps, &ed, &nd));
+    alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+    memset(pbuf, 0, sizeof pbuf);   // the struct holds a union without a default constructor
+    cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(pbuf);
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = s->cond_handle;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    QHP_CUDA(cudaGraphAddNode(&node, cg, deps, ed, nd, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    QHP_CUDA(cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    QHP_CUDA(cudaStreamBeginCaptureToGraph(s->aux_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t main = s->stream;
+    s->stream = s->aux_stream;
+    const int64_t before = s->launches;
+    cudaError_t e = launch_rebuild(s);
+    if (e == cudaSuccess) e = launch_integrate_gated(s);
+    s->kernels_per_rebuild = s->launches - before;
+    s->stream = main;
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s->aux_stream, &out);
+    if (e != cudaSuccess) return cuda_fail(e, "rebuild chain capture");
+    QHP_CUDA(e2);
+    return QHP_OK;
+}
+
+int enqueue_step(qhp_system_s* s, bool adqtb);
+
+// Capture one whole step into the system's executable graph.
+int capture_step_graph(qhp_system_s* s, bool adqtb) {
+    invalidate_graph(s);
+    if (!s->aux_stream) QHP_CUDA(cudaStreamCreateWithFlags(&s->aux_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    QHP_CUDA(cudaGraphCreate(&g, 0));
+    cudaError_t e = cudaGraphConditionalHandleCreate(&s->cond_handle, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(s->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "step graph capture start");
+    }
+    const int64_t before = s->launches;
+    s->cond_active = 1;
+    s->kernels_per_rebuild = 0;
+    const int rc = enqueue_step(s, adqtb);
+    s->cond_active = 0;
+    cudaGraph_t g2 = nullptr;
+    e = cudaStreamEndCapture(s->stream, &g2);
+    if (rc != QHP_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return rc != QHP_OK ? rc : cuda_fail(e, "step graph capture end");
+    }
+    s->kernels_per_step = s->launches - before - s->kernels_per_rebuild;
+    s->launches = before;
+    e = cudaGraphInstantiate(&s->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->graph_exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    s->graph_kind = adqtb ? 1 : 0;
+    return QHP_OK;
+}
+
 int enqueue_step(qhp_system_s* s, bool adqtb) {
     // External records become event-record nodes of the captured step graph, so every
     // replay timestamps its stages (a plain record would only add a capture dependency).
@@ -164,8 +238,12 @@ int enqueue_step(qhp_system_s* s, bool adqtb) {
     QHP_CUDA(launch_integrate(s, true, adqtb));
     if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[1], s->stream, cudaEventRecordExternal));
     QHP_CUDA(launch_list_check(s, false));
-    QHP_CUDA(launch_rebuild(s));
-    QHP_CUDA(launch_integrate_gated(s));
+    if (s->cond_active) {
+        TRY(enqueue_rebuild_conditional(s));
+    } else {
+        QHP_CUDA(launch_rebuild(s));
+        QHP_CUDA(launch_integrate_gated(s));
+    }
     if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[2], s->stream, cudaEventRecordExternal));
     QHP_CUDA(launch_forces(s, false));                      // records prof_ev[3] between pair and bonded
     if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[4], s->stream, cudaEventRecordExternal));
@@ -180,16 +258,29 @@ int enqueue_segment_end(qhp_system_s* s, int64_t steps_done) {
     return qtb_generate_segment(s, steps_done / s->n_seg);
 }
 
+// Every (sorted) atom owns a row of row_cap list entries starting at i * row_cap; the
+// rebuild writes each row's length to nbr_count.  Rows are sized from the longest row of
+// the current centroids with 25% + 64 entries of headroom for density fluctuations; a
+// rebuild that would overrun a row raises the list-overflow status instead.
 int ensure_capacity(qhp_system_s* s) {
-    int64_t total = 0;
-    TRY(host_list_size(s, &total));
-    const int64_t need = s->list_mode ? (int64_t)(1.3 * (double)total) + 1024 : total;
-    if (need > s->nbr_cap) {
+    int64_t longest = 0;
+    TRY(host_list_size(s, &longest));
+    int64_t row = s->list_mode ? ((int64_t)(1.25 * (double)longest) + 64 + 7) / 8 * 8 : (int64_t)s->N;
+    if (row < 8) row = 8;
+    if (row * (int64_t)s->N > ((int64_t)1 << 31) - 1) {
+        qhp::set_error("neighbour list too large (%lld rows of %lld entries)", (long long)s->N, (long long)row);
+        return QHP_ERR_NOMEM;
+    }
+    if (row > s->row_cap) {
         // Grow: the old buffer stays owned by the system until destruction.
         int4* p = nullptr;
-        TRY(dalloc(s, &p, (size_t)need));
+        TRY(dalloc(s, &p, (size_t)row * s->N));
         s->nbr = p;
-        s->nbr_cap = need;
+        s->nbr_cap = row * s->N;
+        s->row_cap = (int)row;
+        std::vector<int> start(s->N + 1);
+        for (int i = 0; i <= s->N; ++i) start[i] = i * (int)row;
+        QHP_CUDA(cudaMemcpy(s->nbr_start, start.data(), sizeof(int) * (s->N + 1), cudaMemcpyHostToDevice));
         invalidate_graph(s);
     }
     return QHP_OK;
@@ -231,21 +322,7 @@ int run_steps(qhp_system_s* s, int n, bool adqtb) {
     if (adqtb) {
         // step by step through one captured step graph; segment ends are enqueued by the host
         for (int k = 0; k < n; ++k) {
-            if (!s->graph_exec || s->graph_kind != kind) {
-                invalidate_graph(s);
-                cudaGraph_t g;
-                const int64_t before = s->launches;
-                QHP_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-                int rc = enqueue_step(s, true);
-                cudaError_t e = cudaStreamEndCapture(s->stream, &g);
-                if (rc != QHP_OK) return rc;
-                QHP_CUDA(e);
-                s->kernels_per_step = s->launches - before;
-                s->launches = before;
-                QHP_CUDA(cudaGraphInstantiate(&s->graph_exec, g, 0));
-                cudaGraphDestroy(g);
-                s->graph_kind = kind;
-            }
+            if (!s->graph_exec || s->graph_kind != kind) TRY(capture_step_graph(s, true));
             QHP_CUDA(cudaGraphLaunch(s->graph_exec, s->stream));
             s->launches += s->kernels_per_step;
             s->step += 1;
@@ -254,21 +331,7 @@ int run_steps(qhp_system_s* s, int n, bool adqtb) {
         return post_status(s);
     }
     if (n >= 1) {
-        if (!s->graph_exec || s->graph_kind != kind) {
-            invalidate_graph(s);
-            cudaGraph_t g;
-            const int64_t before = s->launches;
-            QHP_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-            int rc = enqueue_step(s, adqtb);
-            cudaError_t e = cudaStreamEndCapture(s->stream, &g);
-            if (rc != QHP_OK) return rc;
-            QHP_CUDA(e);
-            s->kernels_per_step = s->launches - before;
-            s->launches = before;
-            QHP_CUDA(cudaGraphInstantiate(&s->graph_exec, g, 0));
-            cudaGraphDestroy(g);
-            s->graph_kind = kind;
-        }
+        if (!s->graph_exec || s->graph_kind != kind) TRY(capture_step_graph(s, false));
         for (int k = 0; k < n; ++k) QHP_CUDA(cudaGraphLaunch(s->graph_exec, s->stream));
         s->launches += s->kernels_per_step * n;
     } else {
@@ -396,6 +459,9 @@ int qhp_destroy_system(qhp_sys s) {
     cudaStreamSynchronize(s->stream);
     free_all(s);
     if (s->status_event) cudaEventDestroy(s->status_event);
+    if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
+    for (int k = 0; k < 6; ++k)
+        if (s->prof_ev[k]) cudaEventDestroy(s->prof_ev[k]);
     if (s->status_host) cudaFreeHost(s->status_host);
     if (s->own_stream) cudaStreamDestroy(s->own_stream);
     delete s;
@@ -415,8 +481,9 @@ int qhp_set_forcefield(qhp_sys s, const qhp_ff* ff) {
     s->ff = *ff;
     s->ff_set = true;
     s->r_list = ff->rc + ff->skin;
-    s->n_c = std::max(1, (int)floor(s->L / s->r_list));
-    s->list_mode = (s->n_c >= 3 && s->r_list < 0.5 * s->L) ? 1 : 0;
+    // cells at least r_list/2 wide: every list partner lies within a 5 x 5 x 5 stencil
+    s->n_c = std::max(1, (int)floor(2.0 * s->L / s->r_list));
+    s->list_mode = (s->n_c >= 5 && s->r_list < 0.5 * s->L) ? 1 : 0;
     if (!s->list_mode) s->n_c = 1;
     s->forces_valid = false;
     s->list_valid = false;
@@ -492,9 +559,8 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     TRY(dalloc(s, &s->status, 1));
     TRY(dalloc(s, &s->dev_max, 1));
     TRY(dalloc(s, &s->rebuild_flag, 1));
-    TRY(dalloc(s, &s->nbr_total, 1));
     TRY(dalloc(s, &s->step_ctr, 1));
-    TRY(dalloc(s, &s->rebuild_count, 1));
+    TRY(dalloc(s, &s->rebuild_count, 2));   // [0] all rebuilds, [1] those run inside step graphs
     TRY(dalloc(s, &s->Tmat, (size_t)P * P));
     TRY(dalloc(s, &s->Tproj, (size_t)P * P));
     TRY(dalloc(s, &s->Tmat_f, (size_t)P * P));
@@ -502,6 +568,7 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     TRY(dalloc(s, &s->cent_buf, (size_t)N * 3));
     s->nbr = nullptr;
     s->nbr_cap = 0;
+    s->row_cap = 0;
 
     std::vector<double> m(N), sm(N);
     for (int i = 0; i < N; ++i) {
@@ -516,7 +583,7 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     QHP_CUDA(cudaMemset(s->status, 0, sizeof(unsigned)));
     QHP_CUDA(cudaMemset(s->dev_max, 0, sizeof(unsigned)));
     QHP_CUDA(cudaMemset(s->step_ctr, 0, sizeof(unsigned long long)));
-    QHP_CUDA(cudaMemset(s->rebuild_count, 0, sizeof(unsigned)));
+    QHP_CUDA(cudaMemset(s->rebuild_count, 0, 2 * sizeof(unsigned)));
     QHP_CUDA(cudaMemset(s->fmode, 0, sizeof(double) * NP3));
     TRY(upload_matrices(s));
     if (s->th.kind == QHP_THERMO_ADQTB && P != 1) s->th.kind = QHP_THERMO_PILE;
@@ -739,14 +806,14 @@ int qhp_get_list_pairs(qhp_sys s, int64_t* pairs, int64_t cap, int64_t* count) {
     if (!s->list_valid) TRY(qhp_build_list(s));
     TRY(sync_and_check(s));
     const int N = s->N;
-    std::vector<int> start(N + 1), perm(N);
-    QHP_CUDA(cudaMemcpy(start.data(), s->nbr_start, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost));
+    std::vector<int> cnt(N), perm(N);
+    QHP_CUDA(cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * N, cudaMemcpyDeviceToHost));
     QHP_CUDA(cudaMemcpy(perm.data(), s->perm, sizeof(int) * N, cudaMemcpyDeviceToHost));
-    std::vector<int4> e(start[N]);
-    QHP_CUDA(cudaMemcpy(e.data(), s->nbr, sizeof(int4) * start[N], cudaMemcpyDeviceToHost));
+    std::vector<int4> e((size_t)s->nbr_cap);
+    QHP_CUDA(cudaMemcpy(e.data(), s->nbr, sizeof(int4) * e.size(), cudaMemcpyDeviceToHost));
     int64_t c = 0;
     for (int i = 0; i < N; ++i)
-        for (int k = start[i]; k < start[i + 1]; ++k) {
+        for (int64_t k = (int64_t)i * s->row_cap; k < (int64_t)i * s->row_cap + cnt[i]; ++k) {
             const int a = perm[i], b = perm[e[k].x & 0x7fffffff];   // bit 31 flags an H partner
             if (a < b) {
                 if (pairs && c < cap) {
@@ -773,12 +840,16 @@ int qhp_get_info(qhp_sys s, qhp_info* out) {
     out->n_cells_per_edge = s->n_c;
     if (s->beads_set) {
         cudaStreamSynchronize(s->stream);
-        unsigned rb = 0;
-        int tot = 0;
-        cudaMemcpy(&rb, s->rebuild_count, sizeof rb, cudaMemcpyDeviceToHost);
-        cudaMemcpy(&tot, s->nbr_total, sizeof tot, cudaMemcpyDeviceToHost);
-        out->rebuilds = rb;
+        unsigned rb[2] = {0u, 0u};
+        std::vector<int> cnt(s->N);
+        cudaMemcpy(rb, s->rebuild_count, sizeof rb, cudaMemcpyDeviceToHost);
+        cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * s->N, cudaMemcpyDeviceToHost);
+        int64_t tot = 0;
+        for (int v : cnt) tot += v;
+        out->rebuilds = rb[0];
         out->list_entries = tot;
+        // kernels run inside step-graph conditionals are counted by the device
+        out->kernel_launches = s->launches + (int64_t)rb[1] * s->kernels_per_rebuild;
     }
     return QHP_OK;
 }

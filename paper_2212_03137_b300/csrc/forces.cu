@@ -107,10 +107,16 @@ __device__ __forceinline__ void pair_term(float dx, float dy, float dz, float qq
     }
 }
 
-constexpr int PAIR_WARPS = 4;
+constexpr int PAIR_WARPS = 4;   // warps per block
+
+// Warps that share one atom's list: with many beads (P >= 16) four warps split the list;
+// with few beads one warp takes a whole list (32/P entries per iteration) and a block
+// holds four atoms.
+template <int P>
+__host__ __device__ constexpr int pair_warps_per_atom() { return P >= 16 ? 4 : 1; }
 
 template <int P, bool ALL, bool ENERGY>
-__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const float4* __restrict__ pos, const int* __restrict__ start,
+__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const float4* __restrict__ pos, const int* __restrict__ start, const int* __restrict__ count,
                                                     const int4* __restrict__ nbr, const float* __restrict__ charge_s,
                                                     const int* __restrict__ type_s, const int* __restrict__ perm,
                                                     long long* __restrict__ F, float* __restrict__ epair, PairConsts c,
@@ -118,12 +124,17 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const flo
     constexpr int JPW = P >= 32 ? 1 : 32 / P;
     constexpr int BPL = P > 32 ? P / 32 : 1;
     constexpr int NB = P > 32 ? P : 32;                   // bead slots reduced across warps
+    constexpr int W = pair_warps_per_atom<P>();
+    constexpr int APB = PAIR_WARPS / W;                   // atoms per block
     __shared__ float red[PAIR_WARPS][4][NB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x;                             // one atom per block, PAIR_WARPS warps on its list
+    const int wa = w % W;                                 // this warp's chunk of the atom's list
+    const int i_raw = blockIdx.x * APB + w / W;
+    const bool live = i_raw < N;
+    const int i = live ? i_raw : N - 1;                   // idle warps still reach the barrier
     const int b0 = P >= 32 ? lane : (lane % P);
     const int jsub = P >= 32 ? 0 : lane / P;
-    const bool ok = (*status & ST_LIST_OVERFLOW) == 0u;
+    const bool ok = live && (*status & ST_LIST_OVERFLOW) == 0u;
     // N * P < 2^30 is checked at set-up, so 32-bit element offsets suffice
     const float4* __restrict__ pl = pos + b0;
 
@@ -139,10 +150,10 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const flo
     const float qi = charge_s[i];
     const bool Oi = type_s[i] == 0;
     const float qO = qi * c.qO_ke, qH = qi * c.qH_ke;
-    // the list of i is cut into PAIR_WARPS contiguous chunks, one per warp
-    const int ka = start[i], kb = ok ? start[i + 1] : start[i];
-    const int chunk = ((kb - ka + PAIR_WARPS - 1) / PAIR_WARPS + JPW - 1) / JPW * JPW;
-    const int kw0 = min(kb, ka + w * chunk), k1 = min(kb, kw0 + chunk);
+    // the list of i is cut into W contiguous chunks, one per warp
+    const int ka = start[i], kb = ok ? ka + count[i] : ka;
+    const int chunk = ((kb - ka + W - 1) / W + JPW - 1) / JPW * JPW;
+    const int kw0 = min(kb, ka + wa * chunk), k1 = min(kb, kw0 + chunk);
     int k = kw0 + jsub;
     // two list entries per iteration: both entries and all their loads are in flight together
     for (; k + JPW < k1; k += 2 * JPW) {
@@ -194,19 +205,19 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const flo
         }
     }
     __syncthreads();
-    // warp 0 adds the chunks in a fixed order and writes each bead force once
-    if (w == 0 && jsub == 0) {
+    // the first warp of each atom adds the chunks in a fixed order and writes each bead force once
+    if (live && wa == 0 && jsub == 0) {
         const int a = perm[i];
 #pragma unroll
         for (int u = 0; u < BPL; ++u) {
             const int b = b0 + 32 * u;
-            float sx = red[0][0][b], sy = red[0][1][b], sz = red[0][2][b], se = red[0][3][b];
+            float sx = red[w][0][b], sy = red[w][1][b], sz = red[w][2][b], se = red[w][3][b];
 #pragma unroll
-            for (int v = 1; v < PAIR_WARPS; ++v) {
-                sx += red[v][0][b];
-                sy += red[v][1][b];
-                sz += red[v][2][b];
-                se += red[v][3][b];
+            for (int v = 1; v < W; ++v) {
+                sx += red[w + v][0][b];
+                sy += red[w + v][1][b];
+                sz += red[w + v][2][b];
+                se += red[w + v][3][b];
             }
             F[((size_t)a * 3 + 0) * P + b] = __float2ll_rn(sx * FIX_SCALE_F);
             F[((size_t)a * 3 + 1) * P + b] = __float2ll_rn(sy * FIX_SCALE_F);
@@ -218,7 +229,8 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const flo
 
 template <bool ENERGY>
 __global__ void __launch_bounds__(128) k_pair_fp64(int N, int P, const double* __restrict__ pos,
-                                                   const int* __restrict__ start, const int4* __restrict__ nbr,
+                                                   const int* __restrict__ start, const int* __restrict__ count,
+                                                   const int4* __restrict__ nbr,
                                                    const float* __restrict__ charge_s, const int* __restrict__ type_s,
                                                    const int* __restrict__ perm, const double q_O, const double q_H,
                                                    double* __restrict__ F, double* __restrict__ epair, PairConsts c,
@@ -235,7 +247,7 @@ __global__ void __launch_bounds__(128) k_pair_fp64(int N, int P, const double* _
     const bool ok = (*status & ST_LIST_OVERFLOW) == 0u;
     const double qi = (type_s[i] == 0 ? q_O : q_H) * c.ke_d;
     const bool Oi = type_s[i] == 0;
-    const int k0 = start[i], k1 = ok ? start[i + 1] : start[i];
+    const int k0 = start[i], k1 = ok ? k0 + count[i] : k0;
     for (int u = 0; u < BPL; ++u) {
         const int b = b0 + 32 * u;
         const double xi = pos[((size_t)0 * N + i) * P + b];
@@ -372,6 +384,7 @@ __global__ void k_bonded(int n_mol, int N, int P, const float4* __restrict__ pos
 // Count in-cutoff bead pairs j > i (lane = bead, one list entry at a time); not on the step path.
 __global__ void k_count_pairs(int N, int P, int mixed, int all, const float4* __restrict__ pos_f,
                               const double* __restrict__ pos_d, const int* __restrict__ start,
+                              const int* __restrict__ count,
                               const int4* __restrict__ nbr, const int* __restrict__ type_s, PairConsts c,
                               unsigned long long* out2) {
     const int lane = threadIdx.x & 31;
@@ -379,7 +392,7 @@ __global__ void k_count_pairs(int N, int P, int mixed, int all, const float4* __
     if (i >= N) return;
     unsigned long long n = 0, noo = 0;
     for (int b = lane; b < P; b += 32) {
-        for (int k = start[i]; k < start[i + 1]; ++k) {
+        for (int k = start[i]; k < start[i] + count[i]; ++k) {
             const int4 e = nbr[k];
             const int j = entry_j(e.x);
             if (j <= i) continue;
@@ -455,23 +468,25 @@ PairConsts make_pair_consts(const qhp_system_s* s) {
 }
 
 template <int P>
-void pair_mixed_dispatch(qhp_system_s* s, bool energy, const PairConsts& c, int grid) {
+void pair_mixed_dispatch(qhp_system_s* s, bool energy, const PairConsts& c, int /*unused*/) {
+    constexpr int apb = PAIR_WARPS / pair_warps_per_atom<P>();
+    const int grid = (s->N + apb - 1) / apb;
     if (s->list_mode) {
         if (energy)
-            k_pair_mixed<P, false, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr, s->charge_s,
+            k_pair_mixed<P, false, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
                                                                       s->type_s, s->perm, s->Ffix, s->e_pair, c,
                                                                       s->status);
         else
-            k_pair_mixed<P, false, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr,
+            k_pair_mixed<P, false, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr,
                                                                        s->charge_s, s->type_s, s->perm, s->Ffix,
                                                                        s->e_pair, c, s->status);
     } else {
         if (energy)
-            k_pair_mixed<P, true, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr, s->charge_s,
+            k_pair_mixed<P, true, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
                                                                      s->type_s, s->perm, s->Ffix, s->e_pair, c,
                                                                      s->status);
         else
-            k_pair_mixed<P, true, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr,
+            k_pair_mixed<P, true, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr,
                                                                       s->charge_s, s->type_s, s->perm, s->Ffix,
                                                                       s->e_pair, c, s->status);
     }
@@ -496,11 +511,11 @@ cudaError_t launch_pair(qhp_system_s* s, bool energy) {
         }
     } else {
         if (energy)
-            k_pair_fp64<true><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr, s->charge_s,
+            k_pair_fp64<true><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
                                                            s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O, s->Fd,
                                                            s->e_pair_d, c, s->status);
         else
-            k_pair_fp64<false><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr, s->charge_s,
+            k_pair_fp64<false><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
                                                             s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O, s->Fd,
                                                             s->e_pair_d, c, s->status);
     }
@@ -539,7 +554,7 @@ cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2) {
     const PairConsts c = make_pair_consts(s);
     const int grid = (s->N * 32 + 127) / 128;
     k_count_pairs<<<grid, 128, 0, s->stream>>>(s->N, s->P, s->precision == QHP_MIXED, s->list_mode, s->pos_f4, s->pos_d,
-                                               s->nbr_start, s->nbr, s->type_s, c, out2);
+                                               s->nbr_start, s->nbr_count, s->nbr, s->type_s, c, out2);
     s->launches += 1;
     return cudaGetLastError();
 }

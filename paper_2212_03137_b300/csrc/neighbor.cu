@@ -12,6 +12,8 @@
 // with each operation rounded on its own (explicit _rn intrinsics, no FMA).  An
 // FP32 prefilter on wrapped centroids decides the candidates that are more than
 // 1e-3 A away from r_list; the rest get the exact FP64 test above.
+#include <vector>
+
 #include "qhp_internal.cuh"
 
 namespace qhp {
@@ -56,15 +58,20 @@ __device__ __forceinline__ int cell_coord(double C, double L, int n_c, double* f
     return c < n_c - 1 ? c : n_c - 1;
 }
 
-// Clear the cell counters and the deviation maximum if a rebuild is due.
+// Decide whether the list must be rebuilt; clear the deviation maximum if so.  Inside a
+// step graph the decision also drives the conditional node that holds the rebuild chain.
 __global__ void k_check(unsigned* dev_max, float thr2, int* flag, int force, unsigned* rebuild_count,
-                        const unsigned* status) {
+                        cudaGraphConditionalHandle cond, int use_cond) {
     const float dmax = __uint_as_float(*dev_max);
     const int rebuild = force || !(dmax <= thr2);   // NaN also triggers a rebuild
     *flag = rebuild;
     if (rebuild) {
         *dev_max = 0u;
         *rebuild_count += 1u;
+    }
+    if (use_cond) {
+        cudaGraphSetConditional(cond, rebuild ? 1u : 0u);
+        if (rebuild) rebuild_count[1] += 1u;   // rebuild chains run inside the step graph
     }
 }
 
@@ -217,9 +224,9 @@ __global__ void k_list(const int* flag, int N, double L, int n_c, double r2max, 
     const float Lf = (float)L;
     int cnt = 0;
     const int base = FILL ? start[i] : 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
+    for (int dz = -2; dz <= 2; ++dz)
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
                 int x = cx + dx, y = cy + dy, z = cz + dz;
                 float sx = 0.f, sy = 0.f, sz = 0.f;
                 if (x < 0) { x += n_c; sx = -Lf; } else if (x >= n_c) { x -= n_c; sx = Lf; }
@@ -264,10 +271,163 @@ __global__ void k_list(const int* flag, int N, double L, int n_c, double r2max, 
     if (!FILL && lane == 0) count[i] = cnt;
 }
 
+// Centroid Verlet list, one block per cell: the 125 stencil cells' candidates are staged
+// in shared memory (in stencil order, ascending index within a cell, i.e. the same order as
+// the per-atom scan) and every atom of the cell tests them from there.
+constexpr int LC_THREADS = 128;
+constexpr int LC_CHUNK = 768;   // 3 x 768 x 16 B of staged candidates: within the 48 KB static limit
+
+template <bool FILL>
+__global__ void __launch_bounds__(LC_THREADS) k_list_cells(
+    const int* flag, int N, double L, int n_c, double r2max, float lo2, float hi2, const int* perm,
+    const int* cell_start, const float4* cw, const float4* cwl, const int* mol_s, const int* type_s,
+    const double* anchor, int* count, const int* start, int4* nbr, int row_cap, unsigned* status) {
+    if (!*flag) return;
+    __shared__ int c_beg[125], c_cnt[125], c_off[126];
+    __shared__ float c_sx[125], c_sy[125], c_sz[125];
+    __shared__ float4 s_w[LC_CHUNK];     // shifted wrapped centroid (prefilter), .w = mol as int bits
+    __shared__ float4 s_l[LC_CHUNK];     // low parts, .w = j | H bit as int bits
+    __shared__ float4 s_s[LC_CHUNK];     // unshifted wrapped centroid (hi), .w = periodic shift code
+    const int c = blockIdx.x;
+    const int i0 = cell_start[c], i1 = cell_start[c + 1];
+    if (i0 == i1) return;
+    const int cx = c % n_c, cy = (c / n_c) % n_c, cz = c / (n_c * n_c);
+    const float Lf = (float)L;
+    const float Llo = (float)(L - (double)Lf);
+    const int t = threadIdx.x;
+    if (t < 125) {
+        const int dx = t % 5 - 2, dy = (t / 5) % 5 - 2, dz = t / 25 - 2;   // stencil order dz, dy, dx
+        int x = cx + dx, y = cy + dy, z = cz + dz;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        if (x < 0) { x += n_c; sx = -Lf; } else if (x >= n_c) { x -= n_c; sx = Lf; }
+        if (y < 0) { y += n_c; sy = -Lf; } else if (y >= n_c) { y -= n_c; sy = Lf; }
+        if (z < 0) { z += n_c; sz = -Lf; } else if (z >= n_c) { z -= n_c; sz = Lf; }
+        const int cj = (z * n_c + y) * n_c + x;
+        c_beg[t] = cell_start[cj];
+        c_cnt[t] = cell_start[cj + 1] - c_beg[t];
+        c_sx[t] = sx;
+        c_sy[t] = sy;
+        c_sz[t] = sz;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int o = 0;
+        for (int k = 0; k < 125; ++k) {
+            c_off[k] = o;
+            o += c_cnt[k];
+        }
+        c_off[125] = o;
+    }
+    __syncthreads();
+    const int M = c_off[125];
+    const int lane = t & 31, w = t >> 5;
+    // per-warp state for up to ceil(atoms in cell / 4) atoms is kept across chunks
+    constexpr int MAXA = 16;   // atoms per warp handled in one pass; more are done in further passes
+    for (int ib = i0; ib < i1; ib += 4 * MAXA) {
+        int cnt[MAXA];
+#pragma unroll
+        for (int a = 0; a < MAXA; ++a) cnt[a] = 0;
+        for (int m0 = 0; m0 < M; m0 += LC_CHUNK) {
+            const int mc = min(LC_CHUNK, M - m0);
+            __syncthreads();
+            for (int e = t; e < mc; e += LC_THREADS) {
+                const int m = m0 + e;
+                int k = 0;   // stencil cell of candidate m (binary search over 125 offsets)
+                int lo = 0, hi = 124;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (c_off[mid] <= m) lo = mid;
+                    else hi = mid - 1;
+                }
+                k = lo;
+                const int j = c_beg[k] + (m - c_off[k]);
+                const float4 wj = cw[j];
+                const float4 lj = cwl[j];
+                const float sx = c_sx[k], sy = c_sy[k], sz = c_sz[k];
+                s_w[e] = make_float4(wj.x + sx, wj.y + sy, wj.z + sz, __int_as_float(mol_s[j]));
+                s_l[e] = make_float4(lj.x, lj.y, lj.z, __int_as_float(j | (type_s[j] ? (int)0x80000000u : 0)));
+                const int code = (sx > 0.f ? 2 : (sx < 0.f ? 0 : 1)) + 3 * (sy > 0.f ? 2 : (sy < 0.f ? 0 : 1)) +
+                                 9 * (sz > 0.f ? 2 : (sz < 0.f ? 0 : 1));
+                s_s[e] = make_float4(wj.x, wj.y, wj.z, __int_as_float(code));
+            }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < MAXA; ++a) {
+                const int i = ib + w + 4 * a;
+                if (i >= i1) break;
+                const float4 wi = cw[i];
+                const int mi = mol_s[i];
+                const int ai = perm[i];
+                int base = 0, lim = 0;
+                float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (FILL) {
+                    base = start[i] + cnt[a];
+                    lim = start[i] + row_cap;
+                    li = cwl[i];
+                }
+                for (int eb = 0; eb < mc; eb += 32) {
+                    const int e = eb + lane;
+                    bool acc = false;
+                    float4 sw = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < mc) {
+                        sw = s_w[e];
+                        if (__float_as_int(sw.w) != mi) {
+                            const float ddx = sw.x - wi.x, ddy = sw.y - wi.y, ddz = sw.z - wi.z;
+                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            if (r2 < lo2) {
+                                acc = true;
+                            } else if (r2 <= hi2) {   // borderline: the exact FP64 definition decides
+                                const int j = __float_as_int(s_l[e].w) & 0x7fffffff;
+                                const int aj = perm[j];
+                                const double ex = min_image_rn(__dsub_rn(anchor[aj * 3], anchor[ai * 3]), L);
+                                const double ey = min_image_rn(__dsub_rn(anchor[aj * 3 + 1], anchor[ai * 3 + 1]), L);
+                                const double ez = min_image_rn(__dsub_rn(anchor[aj * 3 + 2], anchor[ai * 3 + 2]), L);
+                                const double d2 =
+                                    __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                                acc = d2 < r2max;
+                            }
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, acc);
+                    if (FILL && acc) {
+                        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+                        if (pos < lim) {
+                            const float4 sl = s_l[e];
+                            const float4 wj = s_s[e];
+                            const int code = __float_as_int(wj.w);
+                            const float kx = (float)(code % 3 - 1), ky = (float)((code / 3) % 3 - 1),
+                                        kz = (float)(code / 9 - 1);
+                            const float Dx = sep_df(wj.x, sl.x, wi.x, li.x, kx * Lf, kx * Llo);
+                            const float Dy = sep_df(wj.y, sl.y, wi.y, li.y, ky * Lf, ky * Llo);
+                            const float Dz = sep_df(wj.z, sl.z, wi.z, li.z, kz * Lf, kz * Llo);
+                            nbr[pos] = make_int4(__float_as_int(sl.w), __float_as_int(Dx), __float_as_int(Dy),
+                                                 __float_as_int(Dz));
+                        }
+                    }
+                    const int nacc = __popc(bal);
+                    base += nacc;
+                    cnt[a] += nacc;
+                }
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < MAXA; ++a) {
+                const int i = ib + w + 4 * a;
+                if (i < i1) {
+                    // a row is never longer than its slot: an overrun is reported, not read
+                    if (FILL && cnt[a] > row_cap) atomicOr(status, ST_LIST_OVERFLOW);
+                    count[i] = FILL ? min(cnt[a], row_cap) : cnt[a];
+                }
+            }
+        }
+    }
+}
+
 // All pairs of different molecules (small boxes), warp per atom, identity order.
 template <bool FILL>
 __global__ void k_list_all(const int* flag, int N, double L, const int* mol_s, const int* type_s, const double* anchor,
-                           int* count, const int* start, int4* nbr, int64_t cap) {
+                           int* count, const int* start, int4* nbr, int row_cap, unsigned* status) {
     if (!*flag) return;
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -280,8 +440,8 @@ __global__ void k_list_all(const int* flag, int N, double L, const int* mol_s, c
         const bool acc = j < N && mol_s[j] != mi;
         const unsigned bal = __ballot_sync(0xffffffffu, acc);
         if (FILL && acc) {
-            const int64_t pos = (int64_t)base + cnt + __popc(bal & ((1u << lane) - 1u));
-            if (pos < cap) {
+            const int pos = base + cnt + __popc(bal & ((1u << lane) - 1u));
+            if (pos < base + row_cap) {
                 const double iL = 1.0 / L;
                 const float Dx = (float)min_image_fast(anchor[j * 3] - anchor[i * 3], L, iL);
                 const float Dy = (float)min_image_fast(anchor[j * 3 + 1] - anchor[i * 3 + 1], L, iL);
@@ -292,7 +452,10 @@ __global__ void k_list_all(const int* flag, int N, double L, const int* mol_s, c
         }
         cnt += __popc(bal);
     }
-    if (!FILL && lane == 0) count[i] = cnt;
+    if (lane == 0) {
+        if (FILL && cnt > row_cap) atomicOr(status, ST_LIST_OVERFLOW);
+        count[i] = FILL ? min(cnt, row_cap) : cnt;
+    }
 }
 
 }  // namespace
@@ -301,7 +464,7 @@ cudaError_t launch_list_check(qhp_system_s* s, bool force) {
     const float half = (float)(0.5 * s->ff.skin);
     s->launches++;
     k_check<<<1, 1, 0, s->stream>>>(s->dev_max, half * half, s->rebuild_flag, force ? 1 : 0, s->rebuild_count,
-                                    s->status);
+                                    s->cond_handle, s->cond_active);
     return cudaGetLastError();
 }
 
@@ -331,27 +494,21 @@ cudaError_t launch_rebuild(qhp_system_s* s) {
     const int wb = 128, gW = (N * 32 + wb - 1) / wb;
     const double r2max = s->r_list * s->r_list;
     const float lo = (float)(s->r_list - 1e-3), hi = (float)(s->r_list + 1e-3);
+    // one pass: every atom owns a fixed row of row_cap entries, its length goes to nbr_count
     if (s->list_mode) {
-        k_list<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
-                                         s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+        k_list_cells<true><<<ncell, LC_THREADS, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm,
+                                                         s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor,
+                                                         s->nbr_count, s->nbr_start, s->nbr, s->row_cap, s->status);
     } else {
-        k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+        k_list_all<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, s->nbr_start,
+                                            s->nbr, s->row_cap, s->status);
     }
-    k_scan<<<1, 1024, 0, st>>>(flag, s->nbr_count, s->nbr_start, N, s->nbr_cap, s->nbr_total, s->status);
-    if (s->list_mode) {
-        k_list<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
-                                        s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor, nullptr, s->nbr_start, s->nbr,
-                                        s->nbr_cap);
-    } else {
-        k_list_all<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, nullptr, s->nbr_start, s->nbr,
-                                            s->nbr_cap);
-    }
-    s->launches += 4;
+    s->launches += 2;
     return cudaGetLastError();
 }
 
-// Count the list entries for the current centroids (synchronous; sizes the buffer).
-int host_list_size(qhp_system_s* s, int64_t* total) {
+// Row lengths of the list for the current centroids (synchronous; sizes the rows).
+int host_list_size(qhp_system_s* s, int64_t* max_row) {
     int one = 1;
     QHP_CUDA(cudaMemcpyAsync(s->rebuild_flag, &one, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     const int N = s->N;
@@ -378,17 +535,20 @@ int host_list_size(qhp_system_s* s, int64_t* total) {
     const double r2max = s->r_list * s->r_list;
     const float lo = (float)(s->r_list - 1e-3), hi = (float)(s->r_list + 1e-3);
     if (s->list_mode)
-        k_list<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm, s->cell,
-                                         s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
+        k_list_cells<false><<<ncell, LC_THREADS, 0, st>>>(flag, N, s->L, s->n_c, r2max, lo * lo, hi * hi, s->perm,
+                                                          s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor,
+                                                          s->nbr_count, nullptr, nullptr, 0, s->status);
     else
-        k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr, nullptr, 0);
-    k_scan<<<1, 1024, 0, st>>>(flag, s->nbr_count, s->nbr_start, N, -1, s->nbr_total, s->status);
-    s->launches += 10;
+        k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr,
+                                             nullptr, 0, s->status);
+    s->launches += 9;
     QHP_CUDA(cudaGetLastError());
-    int t = 0;
-    QHP_CUDA(cudaMemcpyAsync(&t, s->nbr_total, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<int> cnt(N);
+    QHP_CUDA(cudaMemcpyAsync(cnt.data(), s->nbr_count, sizeof(int) * N, cudaMemcpyDeviceToHost, s->stream));
     QHP_CUDA(cudaStreamSynchronize(s->stream));
-    *total = t;
+    int m = 0;
+    for (int v : cnt) m = v > m ? v : m;
+    *max_row = m;
     return QHP_OK;
 }
 

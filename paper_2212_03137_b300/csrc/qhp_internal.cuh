@@ -152,10 +152,11 @@ struct qhp_system_s {
     int *cell = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr, *tmp_idx = nullptr;
     float4* cw = nullptr;                                    // sorted wrapped centroids (FP32) for the prefilter
     float4* cwl = nullptr;                                   // their low parts: wrapped = cw + cwl (double-float)
-    int* nbr_start = nullptr;                                // [N+1]
-    int* nbr_count = nullptr;                                // [N]
+    int* nbr_start = nullptr;                                // [N+1], row i starts at i * row_cap
+    int* nbr_count = nullptr;                                // [N] row lengths
     int4* nbr = nullptr;                                     // entries {j, Dx, Dy, Dz}
-    int64_t nbr_cap = 0;
+    int64_t nbr_cap = 0;                                     // N * row_cap
+    int row_cap = 0;                                         // entries per row
     float* e_pair = nullptr;                                 // per (sorted atom, bead) pair energy (mixed)
     double* e_pair_d = nullptr;                              // fp64
     double* e_bond = nullptr;                                // [n_mol][P]
@@ -166,11 +167,13 @@ struct qhp_system_s {
     cudaEvent_t status_event = nullptr;
     unsigned* dev_max = nullptr;                             // max squared deviation (float bits)
     int* rebuild_flag = nullptr;
-    int* nbr_total = nullptr;
     unsigned long long* step_ctr = nullptr;                  // device copy of the step counter
     int64_t rebuilds_host = 0;
     int keep_anchor = 0;           // 1 while a checkpoint restore rebuilds from stored anchors
     int prof_on = 0;               // per-stage events recorded inside each step
+    cudaGraphConditionalHandle cond_handle = 0;   // IF node around the rebuild chain of the step graph
+    int cond_active = 0;           // 1 while capturing a step graph that uses it
+    cudaStream_t aux_stream = nullptr;            // captures the conditional body
     cudaEvent_t prof_ev[6] = {};
     double* cent_buf = nullptr;    // [N][3] centroid gather buffer
     unsigned* rebuild_count = nullptr;
@@ -206,7 +209,8 @@ struct qhp_system_s {
     double fdt_delta_last = 0.0;
 
     // ---- state bookkeeping
-    int64_t kernels_per_step = 0;
+    int64_t kernels_per_step = 0;     // kernels of a captured step outside the rebuild conditional
+    int64_t kernels_per_rebuild = 0;  // kernels inside it
     int64_t step = 0;              // host mirror of the device step counter
     bool forces_valid = false;
     bool list_valid = false;
@@ -242,7 +246,7 @@ cudaError_t launch_bonded(qhp_system_s* s, bool energy);
 cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2);
 cudaError_t launch_gather_centroids(qhp_system_s* s, double* out);
 cudaError_t launch_step_counter(qhp_system_s* s);
-int host_list_size(qhp_system_s* s, int64_t* total);
+int host_list_size(qhp_system_s* s, int64_t* max_row);
 int compute_energy(qhp_system_s* s, qhp_energy* out);
 int beads_fp64(qhp_system_s* s, double* dev_out);
 cudaError_t launch_estimators(qhp_system_s* s, double* partial, int* nblocks);

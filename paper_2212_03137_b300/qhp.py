@@ -89,6 +89,7 @@ _SIGS = {
     "qhp_get_profile": [_VP, _VP],
     "qhp_count_pairs": [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "qhp_estimators_noalloc": [C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP],
+    "qhp_get_list_row": [_VP, C.c_int, _IP, C.c_int, _IP],
 }
 
 
@@ -297,6 +298,16 @@ def qhp_get_list_pairs(h) -> np.ndarray:
     out = np.empty((max(cnt.value, 1), 2), dtype=np.int64)
     _check(lib().qhp_get_list_pairs(h, out.ctypes.data_as(C.POINTER(C.c_int64)), cnt.value, C.byref(cnt)))
     return out[: cnt.value]
+
+
+def qhp_get_list_row(h, atom: int) -> np.ndarray:
+    cnt = C.c_int(0)
+    buf = np.empty(4096, dtype=np.int32)
+    _check(lib().qhp_get_list_row(h, int(atom), _ip(buf), len(buf), C.byref(cnt)))
+    if cnt.value > len(buf):
+        buf = np.empty(cnt.value, dtype=np.int32)
+        _check(lib().qhp_get_list_row(h, int(atom), _ip(buf), len(buf), C.byref(cnt)))
+    return buf[: cnt.value].copy()
 
 
 def qhp_set_stream(h, stream_ptr: int | None) -> None:
