@@ -189,6 +189,13 @@ int qhp_get_profile(qhp_sys sys, qhp_profile* out);
 /* Number of bead pairs (each unordered pair once, summed over beads) within rc
  * at the current positions, and how many of them are O-O (LJ) pairs. */
 int qhp_count_pairs(qhp_sys sys, int64_t* pairs, int64_t* oo_pairs);
+/* Launch mode of qhp_step_rpmd / qhp_step_adqtb.  use_graphs = 1 (default): each
+ * step replays one captured CUDA graph whose list-rebuild chain sits behind a
+ * conditional node.  use_graphs = 0: the same kernels are launched one by one and
+ * the rebuild chain is launched every step, its kernels returning at once when no
+ * rebuild is due (for kernel-by-kernel profilers, which do not see kernels inside
+ * conditional graph bodies).  Results are bit-identical in both modes. */
+int qhp_set_graph_mode(qhp_sys sys, int use_graphs);
 /* Use an external CUDA stream (cudaStream_t passed as void*); NULL restores the
  * library's own stream. */
 int qhp_set_stream(qhp_sys sys, void* stream);

@@ -231,12 +231,12 @@ int capture_step_graph(qhp_system_s* s, bool adqtb) {
 }
 
 int enqueue_step(qhp_system_s* s, bool adqtb) {
-    // External records become event-record nodes of the captured step graph, so every
-    // replay timestamps its stages (a plain record would only add a capture dependency).
+    // Under capture the stage records become event-record nodes, so every replay
+    // timestamps its stages.
     const bool prof = s->prof_on != 0;
-    if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[0], s->stream, cudaEventRecordExternal));
+    if (prof) QHP_CUDA(record_stage(s, 0));
     QHP_CUDA(launch_integrate(s, true, adqtb));
-    if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[1], s->stream, cudaEventRecordExternal));
+    if (prof) QHP_CUDA(record_stage(s, 1));
     QHP_CUDA(launch_list_check(s, false));
     if (s->cond_active) {
         TRY(enqueue_rebuild_conditional(s));
@@ -244,11 +244,11 @@ int enqueue_step(qhp_system_s* s, bool adqtb) {
         QHP_CUDA(launch_rebuild(s));
         QHP_CUDA(launch_integrate_gated(s));
     }
-    if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[2], s->stream, cudaEventRecordExternal));
+    if (prof) QHP_CUDA(record_stage(s, 2));
     QHP_CUDA(launch_forces(s, false));                      // records prof_ev[3] between pair and bonded
-    if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[4], s->stream, cudaEventRecordExternal));
+    if (prof) QHP_CUDA(record_stage(s, 4));
     QHP_CUDA(launch_project(s, true));
-    if (prof) QHP_CUDA(cudaEventRecordWithFlags(s->prof_ev[5], s->stream, cudaEventRecordExternal));
+    if (prof) QHP_CUDA(record_stage(s, 5));
     return QHP_OK;
 }
 
@@ -319,6 +319,14 @@ int run_steps(qhp_system_s* s, int n, bool adqtb) {
     }
     if (n == 0) return QHP_OK;
     const int kind = adqtb ? 1 : 0;
+    if (!s->use_graphs) {
+        for (int k = 0; k < n; ++k) {
+            TRY(enqueue_step(s, adqtb));
+            s->step += 1;
+            if (adqtb && s->step % s->n_seg == 0) TRY(enqueue_segment_end(s, s->step));
+        }
+        return post_status(s);
+    }
     if (adqtb) {
         // step by step through one captured step graph; segment ends are enqueued by the host
         for (int k = 0; k < n; ++k) {
@@ -1043,6 +1051,16 @@ int qhp_set_profiling(qhp_sys s, int on) {
         for (int k = 0; k < 6; ++k) QHP_CUDA(cudaEventCreate(&s->prof_ev[k]));
     if ((on != 0) != (s->prof_on != 0)) invalidate_graph(s);   // events are captured into the step graph
     s->prof_on = on ? 1 : 0;
+    return QHP_OK;
+}
+
+int qhp_set_graph_mode(qhp_sys s, int use_graphs) {
+    if (!s || (use_graphs != 0 && use_graphs != 1)) {
+        set_error("qhp_set_graph_mode: need a system and use_graphs 0 or 1");
+        return QHP_ERR_ARG;
+    }
+    if (use_graphs != s->use_graphs) invalidate_graph(s);
+    s->use_graphs = use_graphs;
     return QHP_OK;
 }
 

@@ -543,7 +543,7 @@ cudaError_t launch_forces(qhp_system_s* s, bool energy) {
     cudaError_t e = launch_pair(s, energy);
     if (e != cudaSuccess) return e;
     if (s->prof_on) {
-        e = cudaEventRecordWithFlags(s->prof_ev[3], s->stream, cudaEventRecordExternal);
+        e = record_stage(s, 3);
         if (e != cudaSuccess) return e;
     }
     return launch_bonded(s, energy);

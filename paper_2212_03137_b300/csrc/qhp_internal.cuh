@@ -171,6 +171,7 @@ struct qhp_system_s {
     int64_t rebuilds_host = 0;
     int keep_anchor = 0;           // 1 while a checkpoint restore rebuilds from stored anchors
     int prof_on = 0;               // per-stage events recorded inside each step
+    int use_graphs = 1;            // 0: launch each step's kernels directly
     cudaGraphConditionalHandle cond_handle = 0;   // IF node around the rebuild chain of the step graph
     int cond_active = 0;           // 1 while capturing a step graph that uses it
     cudaStream_t aux_stream = nullptr;            // captures the conditional body
@@ -229,6 +230,18 @@ int cuda_fail(cudaError_t e, const char* what);
         cudaError_t e_ = (call);                                    \
         if (e_ != cudaSuccess) return ::qhp::cuda_fail(e_, #call);  \
     } while (0)
+
+// Stage timestamp k of the step profile.  Inside a stream capture the record must be an
+// external one to become an event-record node of the graph (a plain record would only add
+// a capture dependency); outside a capture a plain record is the only valid form.
+inline cudaError_t record_stage(qhp_system_s* s, int k) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s->stream, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(s->prof_ev[k], s->stream, cudaEventRecordExternal)
+               : cudaEventRecord(s->prof_ev[k], s->stream);
+}
 
 // ---- kernels (launchers return cudaError_t of the launch)
 struct StepArgs;

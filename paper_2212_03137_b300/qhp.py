@@ -86,6 +86,7 @@ _SIGS = {
     "qhp_get_info": [_VP, C.POINTER(qhp_info)],
     "qhp_set_stream": [_VP, _VP],
     "qhp_set_profiling": [_VP, C.c_int],
+    "qhp_set_graph_mode": [_VP, C.c_int],
     "qhp_get_profile": [_VP, _VP],
     "qhp_count_pairs": [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "qhp_estimators_noalloc": [C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP],
@@ -316,6 +317,10 @@ def qhp_set_stream(h, stream_ptr: int | None) -> None:
 
 def qhp_set_profiling(h, on: bool) -> None:
     _check(lib().qhp_set_profiling(h, 1 if on else 0))
+
+
+def qhp_set_graph_mode(h, use_graphs: bool) -> None:
+    _check(lib().qhp_set_graph_mode(h, 1 if use_graphs else 0))
 
 
 def qhp_get_profile(h) -> qhp_profile:

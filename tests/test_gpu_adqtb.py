@@ -111,6 +111,17 @@ def test_adqtb_checkpoint_resume_mid_segment():
     assert np.array_equal(Q1, Q2) and np.array_equal(P1, P2) and np.array_equal(g1, g2)
 
 
+def test_adqtb_direct_launches_match_step_graphs():
+    with _gpu(CFG) as a, _gpu(CFG) as b:
+        qhp.qhp_set_graph_mode(b.h, False)
+        qhp.qhp_step_adqtb(a.h, 70)                # crosses a segment end
+        qhp.qhp_step_adqtb(b.h, 70)
+        Qa, Pa = qhp.qhp_get_modes(a.h)
+        Qb, Pb = qhp.qhp_get_modes(b.h)
+        assert np.array_equal(Qa, Qb) and np.array_equal(Pa, Pb)
+        assert np.array_equal(qhp.qhp_get_gamma(a.h, CFG.n_seg), qhp.qhp_get_gamma(b.h, CFG.n_seg))
+
+
 def test_adqtb_rejects_bad_segments():
     box = CFG.system()
     h = qhp.qhp_create_system(box.types, box.molecule, box.pos, box.box, qhp.QHP_MIXED)

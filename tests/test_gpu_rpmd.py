@@ -224,6 +224,27 @@ def test_runs_are_bitwise_reproducible_and_checkpoint_resumes():
         assert qhp.qhp_get_info(a.h).step == 21
 
 
+def test_direct_launches_match_step_graphs():
+    """Kernel-by-kernel launches give the same trajectory, bit for bit, as the step graphs."""
+    cfg = SMALL
+    with _sys(cfg) as a, _sys(cfg) as b:
+        qhp.qhp_set_graph_mode(b.h, False)
+        qhp.qhp_step_rpmd(a.h, 30)                 # crosses list rebuilds
+        for _ in range(3):
+            qhp.qhp_step_rpmd(b.h, 10)
+        Qa, Pa = qhp.qhp_get_modes(a.h)
+        Qb, Pb = qhp.qhp_get_modes(b.h)
+        assert np.array_equal(Qa, Qb) and np.array_equal(Pa, Pb)
+        assert qhp.qhp_get_info(a.h).rebuilds == qhp.qhp_get_info(b.h).rebuilds > 1
+        for h in (a.h, b.h):                       # stage timestamps in both modes
+            qhp.qhp_set_profiling(h, True)
+            qhp.qhp_step_rpmd(h, 1)
+            pr = qhp.qhp_get_profile(h)
+            assert pr.pair_ms > 0 and pr.step_ms >= pr.pair_ms
+        with pytest.raises(qhp.QHPError):
+            qhp._check(qhp.lib().qhp_set_graph_mode(a.h, 2))
+
+
 def test_mode_equipartition_under_pile():
     """PILE samples <P_n^2> = m kT on every mode (Eq. (7))."""
     cfg = C1
