@@ -22,7 +22,10 @@ quantum effects", arXiv 2212.03137):
 * ``qtb``           - the adQTB colored noise, spectra and gamma(omega)
   adaptation (Sec. II.B Eqs. (12)-(15); Sec. III.B Eqs. (21)-(26));
 * ``philox``        - Philox4x32-10 (Salmon et al., SC'11) and Box-Muller,
-  the random numbers both sides draw from the same counters.
+  the random numbers both sides draw from the same counters;
+* ``gradients``     - dU_P/dx and dU_P/dtheta (analytic) for the force-field
+  parameters theta = (eps, sigma, q_O, k_b, k_theta), and the gradient of a
+  K-step trajectory average by central differences of whole trajectories.
 
 Parity pins live in ``tests/test_oracle_*.py``.  Parity unpinned: the finite
 time-step behaviour of the adQTB spectrum estimator at omega*dt ~ 1 (the
