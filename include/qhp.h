@@ -107,7 +107,10 @@ int qhp_create_system(qhp_sys* out, int n_atoms, const int* type, const int* mol
                       const double* pos, double box_L, int precision);
 int qhp_destroy_system(qhp_sys sys);
 
-/* Set the potential (copied).  Must precede qhp_set_beads.  rc must be below box_L/2. */
+/* Set the potential (copied).  The first call must precede qhp_set_beads; rc must be
+ * below box_L/2.  Later calls may change eps, sigma, q_O, k_b, r0, k_theta, theta0 and
+ * alpha only (QHP_ERR_STATE otherwise); the next step or force call re-evaluates the
+ * forces with them. */
 int qhp_set_forcefield(qhp_sys sys, const qhp_ff* ff);
 
 /* Allocate the P-bead state and initialise it (Eqs. (4), (7)): Q_0 = input
@@ -189,6 +192,29 @@ int qhp_get_profile(qhp_sys sys, qhp_profile* out);
 /* Number of bead pairs (each unordered pair once, summed over beads) within rc
  * at the current positions, and how many of them are O-O (LJ) pairs. */
 int qhp_count_pairs(qhp_sys sys, int64_t* pairs, int64_t* oo_pairs);
+/* Differentiation (the paper has no counterpart; FP64 kernels in either precision).
+ * theta = (eps, sigma, q_O, k_b, k_theta) of the current force field, q_H = -q_O/2.
+ *
+ * qhp_energy_grad: U_P = (1/P) sum_b V(x_b) (Eq. (3), with the DSF self term) at the
+ * current bead positions, dU_P/dx = -F_b/P as out[P][n_atoms][3] (host, may be NULL)
+ * and dU_P/dtheta[5] (host, may be NULL).  Synchronous.
+ * qhp_energy_grad_device: the same with device arrays; if x (device [P][n_atoms][3])
+ * is not NULL the bead positions first become the system's modes (momenta kept) and the
+ * list is rebuilt around them.  energy and dE_dtheta are host pointers (may be NULL).
+ *
+ * qhp_segment_grad: J = (1/K) sum_{k=1..K} a(Q_k) along K BAOAB steps (Eq. (17)) from
+ * the current state, with the thermostat noise of those steps held fixed, and dJ/dtheta
+ * by the adjoint of the FP64 step (Hessian-vector products of the forces, exact).
+ * observable 0: the potential energy at the centroid V(Q_0); 1: the mean O-H bond
+ * length over beads and both bonds of every molecule.  The forward trajectory is
+ * replayed from host checkpoints taken every `block` steps (device memory for block + 1
+ * mode arrays).  Needs QHP_FP64 and the PILE or NVE thermostat (QHP_ERR_STATE
+ * otherwise); K, block >= 1.  The system is left in the state it had before the call.
+ * Synchronous; J and dJ_dtheta[5] are host pointers. */
+int qhp_energy_grad(qhp_sys sys, double* energy, double* dE_dx, double* dE_dtheta);
+int qhp_energy_grad_device(qhp_sys sys, const double* x, double* energy, double* dE_dx, double* dE_dtheta);
+int qhp_segment_grad(qhp_sys sys, int K, int block, int observable, double* J, double* dJ_dtheta);
+
 /* Launch mode of qhp_step_rpmd / qhp_step_adqtb.  use_graphs = 1 (default): each
  * step replays one captured CUDA graph whose list-rebuild chain sits behind a
  * conditional node.  use_graphs = 0: the same kernels are launched one by one and

@@ -30,20 +30,6 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
-template <typename T>
-int dalloc(qhp_system_s* s, T** p, size_t count) {
-    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) {
-        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-        return QHP_ERR_NOMEM;
-    }
-    *p = static_cast<T*>(q);
-    s->allocs.push_back({q, bytes});
-    return QHP_OK;
-}
-
 void free_all(qhp_system_s* s) {
     if (s->graph_exec) {
         cudaGraphExecDestroy(s->graph_exec);
@@ -58,15 +44,11 @@ void free_all(qhp_system_s* s) {
     s->qtb_H = s->qtb_tw4 = s->qtb_tw2 = nullptr;
     s->qtb_dof_type = nullptr;
     s->n_seg = 0;
+    s->grad = GradBuffers{};
     s->nbr = nullptr;
     s->nbr_cap = 0;
 }
 
-#define TRY(x)                     \
-    do {                           \
-        int rc_ = (x);             \
-        if (rc_ != QHP_OK) return rc_; \
-    } while (0)
 
 // ---------------------------------------------------------------- reductions
 constexpr int RED_BLOCKS = 256;
@@ -97,6 +79,11 @@ __global__ void k_sum_final(const double* part, int n, double* out) {
 int check_status(qhp_system_s* s, unsigned st) {
     if (st & ST_LIST_OVERFLOW) {
         qhp::set_error("neighbour list overflow (a row exceeds its %d entries)", s->row_cap);
+        return QHP_ERR_LIST_OVERFLOW;
+    }
+    if (st & ST_SPREAD) {
+        qhp::set_error("a bead lies farther than skin/2 from its centroid right after a list rebuild: "
+                       "increase the skin");
         return QHP_ERR_LIST_OVERFLOW;
     }
     if (st & ST_NONFINITE) {
@@ -151,6 +138,7 @@ int enqueue_forces(qhp_system_s* s, bool force_rebuild, bool energy) {
     QHP_CUDA(launch_list_check(s, force_rebuild));
     QHP_CUDA(launch_rebuild(s));
     QHP_CUDA(launch_integrate_gated(s));
+    QHP_CUDA(launch_cover_check(s));
     QHP_CUDA(launch_forces(s, energy));
     QHP_CUDA(launch_project(s, false));
     return QHP_OK;
@@ -183,6 +171,7 @@ int enqueue_rebuild_conditional(qhp_system_s* s) {
     const int64_t before = s->launches;
     cudaError_t e = launch_rebuild(s);
     if (e == cudaSuccess) e = launch_integrate_gated(s);
+    if (e == cudaSuccess) e = launch_cover_check(s);
     s->kernels_per_rebuild = s->launches - before;
     s->stream = main;
     cudaGraph_t out = nullptr;
@@ -243,6 +232,7 @@ int enqueue_step(qhp_system_s* s, bool adqtb) {
     } else {
         QHP_CUDA(launch_rebuild(s));
         QHP_CUDA(launch_integrate_gated(s));
+        QHP_CUDA(launch_cover_check(s));
     }
     if (prof) QHP_CUDA(record_stage(s, 2));
     QHP_CUDA(launch_forces(s, false));                      // records prof_ev[3] between pair and bonded
@@ -360,6 +350,16 @@ double self_energy(const qhp_system_s* s) {
 }
 
 }  // namespace
+
+// Rebuild the list around the current modes now (synchronous).  The rebuild chain checks
+// that every bead lies within skin/2 of its anchor and reports QHP_ERR_LIST_OVERFLOW if not.
+int rebuild_list_now(qhp_system_s* s) {
+    TRY(enqueue_forces(s, true, false));
+    TRY(sync_and_check(s));
+    s->forces_valid = true;
+    s->list_valid = true;
+    return QHP_OK;
+}
 
 cudaError_t launch_sum(qhp_system_s* s, const double* xd, const float* xf, int64_t n, double* out) {
     if (xd) k_sum_part<double><<<RED_BLOCKS, 256, 0, s->stream>>>(xd, n, s->red_tmp);
@@ -485,6 +485,10 @@ int qhp_set_forcefield(qhp_sys s, const qhp_ff* ff) {
         ff->alpha < 0.0 || ff->sigma <= 0.0) {
         set_error("force field: need 0 < rc < box/2, skin >= 0, positive masses and sigma, alpha >= 0");
         return QHP_ERR_ARG;
+    }
+    if (s->beads_set && (ff->rc != s->ff.rc || ff->skin != s->ff.skin || ff->m_O != s->ff.m_O || ff->m_H != s->ff.m_H)) {
+        set_error("after qhp_set_beads only eps, sigma, q_O, k_b, r0, k_theta, theta0 and alpha may change");
+        return QHP_ERR_STATE;
     }
     s->ff = *ff;
     s->ff_set = true;

@@ -35,7 +35,6 @@ struct PairConsts {
 
 // List entries carry the partner's sorted index in the low 31 bits and "partner is H"
 // in bit 31, so the partner's charge and LJ flag need no extra load.
-constexpr int ENTRY_H_BIT = (int)0x80000000u;
 __device__ __forceinline__ int entry_j(int x) { return x & 0x7fffffff; }
 __device__ __forceinline__ bool entry_is_h(int x) { return x < 0; }
 

@@ -75,6 +75,13 @@ __global__ void k_check(unsigned* dev_max, float thr2, int* flag, int force, uns
     }
 }
 
+// Right after a rebuild the deviation maximum is measured from the new anchors; the list
+// covers every bead pair within rc only if no bead lies farther than skin/2 from its anchor.
+__global__ void k_check_cover(const int* flag, const unsigned* dev_max, float thr2, unsigned* status) {
+    if (!*flag) return;
+    if (!(__uint_as_float(*dev_max) <= thr2)) atomicOr(status, ST_SPREAD);
+}
+
 __global__ void k_zero_ints(const int* flag, int* a, int n) {
     if (!*flag) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -465,6 +472,13 @@ cudaError_t launch_list_check(qhp_system_s* s, bool force) {
     s->launches++;
     k_check<<<1, 1, 0, s->stream>>>(s->dev_max, half * half, s->rebuild_flag, force ? 1 : 0, s->rebuild_count,
                                     s->cond_handle, s->cond_active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cover_check(qhp_system_s* s) {
+    const float half = (float)(0.5 * s->ff.skin);
+    s->launches++;
+    k_check_cover<<<1, 1, 0, s->stream>>>(s->rebuild_flag, s->dev_max, half * half, s->status);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ enum : unsigned {
     ST_LIST_OVERFLOW = 1u,
     ST_NONFINITE = 2u,
     ST_TIMEOUT = 4u,
+    ST_SPREAD = 8u,   // after a rebuild some bead lies farther than skin/2 from its anchor
 };
 
 // Philox4x32-10 counter tags (same definition as the oracle, written independently).
@@ -110,6 +111,24 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+}  // namespace qhp
+
+namespace qhp {
+// Device buffers of the gradient entry points (allocated on first use, freed with the system).
+struct GradBuffers {
+    bool ready = false;
+    double *x = nullptr, *v = nullptr;          // bead positions and tangents, [3][N][P] sorted
+    double *F = nullptr, *Ft = nullptr;         // forces and their tangents, [3][N][P] sorted
+    double *part = nullptr, *partb = nullptr;   // per (atom, bead) / (molecule, bead) partial sums
+    double *x1 = nullptr, *F1 = nullptr;        // one-bead (centroid) configuration, [3][N]
+    double *part1 = nullptr, *partb1 = nullptr;
+    double *G = nullptr, *parto = nullptr;      // observable gradient [3][N][P], per (molecule, bead) values
+    double *lamQ = nullptr, *lamP = nullptr;    // adjoints of the modes and momenta, [N][3][P]
+    double* Qbuf = nullptr;                     // modes of one recomputed block, [(block + 1)][N][3][P]
+    int qbuf_steps = 0;
+    double* sums = nullptr;                     // column sums [16]
+    double* acc = nullptr;                      // device accumulators: [0] J, [1..5] dJ/dtheta
+};
 }  // namespace qhp
 
 struct qhp_system_s {
@@ -219,12 +238,34 @@ struct qhp_system_s {
     int graph_kind = -1;
 
     std::vector<qhp::DevBuf> allocs;
+    qhp::GradBuffers grad;
 };
 
 namespace qhp {
 
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+
+// Device allocation owned by the system (freed in qhp_destroy_system or on re-initialisation).
+template <typename T>
+int dalloc(qhp_system_s* s, T** p, size_t count) {
+    const size_t bytes = (count > 0 ? count : 1) * sizeof(T);
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return QHP_ERR_NOMEM;
+    }
+    *p = static_cast<T*>(q);
+    s->allocs.push_back({q, bytes});
+    return QHP_OK;
+}
+#define TRY(x)                         \
+    do {                               \
+        const int rc_ = (x);           \
+        if (rc_ != QHP_OK) return rc_; \
+    } while (0)
+
 #define QHP_CUDA(call)                                              \
     do {                                                            \
         cudaError_t e_ = (call);                                    \
@@ -253,6 +294,7 @@ int qtb_setup(qhp_system_s* s);
 cudaError_t launch_project(qhp_system_s* s, bool kick);
 cudaError_t launch_list_check(qhp_system_s* s, bool force);
 cudaError_t launch_rebuild(qhp_system_s* s);
+cudaError_t launch_cover_check(qhp_system_s* s);   // after a rebuild: every bead within skin/2
 cudaError_t launch_forces(qhp_system_s* s, bool energy);
 cudaError_t launch_pair(qhp_system_s* s, bool energy);
 cudaError_t launch_bonded(qhp_system_s* s, bool energy);
@@ -260,6 +302,7 @@ cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2);
 cudaError_t launch_gather_centroids(qhp_system_s* s, double* out);
 cudaError_t launch_step_counter(qhp_system_s* s);
 int host_list_size(qhp_system_s* s, int64_t* max_row);
+int rebuild_list_now(qhp_system_s* s);   // synchronous; checks the beads are covered
 int compute_energy(qhp_system_s* s, qhp_energy* out);
 int beads_fp64(qhp_system_s* s, double* dev_out);
 cudaError_t launch_estimators(qhp_system_s* s, double* partial, int* nblocks);

@@ -91,6 +91,9 @@ _SIGS = {
     "qhp_count_pairs": [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "qhp_estimators_noalloc": [C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP],
     "qhp_get_list_row": [_VP, C.c_int, _IP, C.c_int, _IP],
+    "qhp_energy_grad": [_VP, _DP, _DP, _DP],
+    "qhp_energy_grad_device": [_VP, _VP, _DP, _VP, _DP],
+    "qhp_segment_grad": [_VP, C.c_int, C.c_int, C.c_int, _DP, _DP],
 }
 
 
@@ -345,6 +348,49 @@ def qhp_count_pairs(h) -> tuple[int, int]:
 
 # ------------------------------------------------------------------ convenience
 
+PARAM_NAMES = ("eps", "sigma", "q_O", "k_b", "k_theta")
+
+
+def qhp_energy_grad(h):
+    """(U_P, dU_P/dx [P, N, 3], dU_P/dtheta [5]) at the current bead positions."""
+    N, P = _dims(h)
+    e = C.c_double(0.0)
+    gx = np.empty((P, N, 3))
+    gt = np.empty(5)
+    _check(lib().qhp_energy_grad(h, C.byref(e), _dp(gx), _dp(gt)))
+    return e.value, gx, gt
+
+
+def qhp_energy_grad_device(h, x_ptr: int | None, gx_ptr: int | None, want_theta: bool = True):
+    """Device variant: x_ptr / gx_ptr are device addresses of [P, N, 3] FP64 arrays (or None)."""
+    e = C.c_double(0.0)
+    gt = np.empty(5)
+    _check(lib().qhp_energy_grad_device(h, C.c_void_p(x_ptr or 0), C.byref(e), C.c_void_p(gx_ptr or 0),
+                                        _dp(gt) if want_theta else None))
+    return e.value, gt
+
+
+def qhp_segment_grad(h, K: int, block: int, observable: int):
+    """(J, dJ/dtheta [5]) of the K-step time average of observable 0 (centroid V) or 1 (mean O-H)."""
+    J = C.c_double(0.0)
+    g = np.empty(5)
+    _check(lib().qhp_segment_grad(h, int(K), int(block), int(observable), C.byref(J), _dp(g)))
+    return J.value, g
+
+
+def ff_with_params(ff: qhp_ff, theta) -> qhp_ff:
+    """Copy of ff with (eps, sigma, q_O, k_b, k_theta) replaced."""
+    out = qhp_ff()
+    C.pointer(out)[0] = ff
+    for n, v in zip(PARAM_NAMES, theta):
+        setattr(out, n, float(v))
+    return out
+
+
+def ff_params(ff: qhp_ff) -> np.ndarray:
+    return np.array([getattr(ff, n) for n in PARAM_NAMES], dtype=float)
+
+
 def make_ff(rc: float, skin: float = 2.0, **kw) -> qhp_ff:
     from .workloads import WATER_FF as W
     p = dict(eps=W["eps"], sigma=W["sigma"], q_O=W["q_O"], k_b=W["k_b"], r0=W["r0"], k_theta=W["k_theta"],
@@ -377,6 +423,12 @@ class System:
             raise
         self.n_atoms, self.P = len(types), P
         self.thermo = thermo
+        self.ff = ff
+
+    def set_params(self, theta) -> None:
+        """Replace (eps, sigma, q_O, k_b, k_theta) of the force field."""
+        self.ff = ff_with_params(self.ff, theta)
+        qhp_set_forcefield(self.h, self.ff)
 
     @classmethod
     def from_config(cls, cfg, precision=None, **over):
