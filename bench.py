@@ -255,6 +255,132 @@ def run_ours(args, ws, rank, local):
     return out
 
 
+def run_batch(args, ws, rank, local):
+    """256 independent boxes (64-2,048 waters, P from {4..64}) stepped by the batched launches."""
+    import torch
+    from paper_2212_03137_b300 import build, qhp
+    from paper_2212_03137_b300.workloads import batch_configs
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfgs = batch_configs(seed=1234 + 1000 * rank)
+    systems = [qhp.System.from_config(c) for c in cfgs]
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    b = qhp.Batch(systems)
+    qhp.qhp_batch_set_stream(b.h, stream.cuda_stream)
+    tuned = qhp.qhp_batch_autotune(b.h, 3)
+    units_step = sum(s.n_atoms * s.P for s in systems)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        b.step(1)
+    b.sync()
+    pairs = oo = 0
+    for s in systems:
+        p_, o_ = qhp.qhp_count_pairs(s.h)
+        pairs += p_
+        oo += o_
+    dist = ws > 1
+    if dist:
+        import torch.distributed as td
+        td.barrier()
+    torch.cuda.synchronize(dev)
+    i0 = qhp.qhp_batch_get_info(b.h)
+    step_ms, stages = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            b.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            pr = qhp.qhp_batch_get_profile(b.h)
+            stages.append([pr.integrate_ms, pr.list_ms, pr.pair_ms, pr.bonded_ms, pr.project_ms])
+    b.sync()
+    i1 = qhp.qhp_batch_get_info(b.h)
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        import torch.distributed as td
+        t = torch.tensor([total_ms], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        total_ms = float(t.item())
+        td.barrier()
+    value = units_step * args.steps * ws / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+    out = None
+    if rank == 0:
+        peaks, src = _peaks()
+        smax = float(peaks.get("sm_max_mhz", 2032.0))
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_tflops = n_sm * 128 * 2 * smax * 1e6 / 1e12
+        st = np.mean(np.array(stages), axis=0)
+        flops = FLOPS_PAIR * pairs + FLOPS_LJ * oo
+        achieved = flops / (st[2] * 1e-3) / 1e12
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/i64/f64 (mixed)", "data": "synthetic",
+            "ns_per_day": 1e3 / ms_per_step * 0.5 * 86400.0 / 1e6,
+            "config": {"workload": "batch_256", "n_systems": len(cfgs), "atom_beads_per_step": units_step,
+                       "n_molecules_range": [min(c.n_mol for c in cfgs), max(c.n_mol for c in cfgs)],
+                       "beads": sorted({c.P for c in cfgs}), "density_g_cm3": 1.0, "dt_fs": 0.5,
+                       "temperature_K": 300.0, "thermostat": "pile", "precision": "mixed",
+                       "tuned_warps_per_atom": {str(k): v for k, v in tuned.items()},
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}",
+                       "launch": "one CUDA graph per batched step"},
+            "roofline": {"kernel": "batched nonbonded pair kernel", "bound": "alu", "achieved": achieved,
+                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": _profile_traffic("pair", "batch_256"), "pairs_per_launch": pairs,
+                         "oo_pairs_per_launch": oo, "flops_per_launch": flops, "mean_launch_ms": float(st[2]),
+                         "share_of_step": float(st[2]) / ms_per_step,
+                         "peak_source": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} clock)"},
+            "clocks": clk.summary(),
+            "gpu_launches": int(i1.kernel_launches - i0.kernel_launches),
+            "stage_ms": dict(zip(["integrate_transform", "list_check_rebuild", "pair", "bonded", "project_kick"],
+                                 [round(float(x), 5) for x in st])),
+            "list_rebuilds": int(i1.rebuilds - i0.rebuilds),
+        }
+    if args.e2e:
+        # public API with host buffers: every box's momenta uploaded from pinned memory,
+        # one batched step, every box's centroids read back
+        import torch as _t
+        pins = [_t.from_numpy(qhp.qhp_get_modes(s.h)[1]).pin_memory() for s in systems]
+        cents = [np.empty((s.n_atoms, 3)) for s in systems]
+        n = max(1, min(args.steps, 20))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(n):
+            for s, pin in zip(systems, pins):
+                qhp.lib().qhp_set_modes(s.h, None, qhp.C.cast(pin.data_ptr(), qhp._DP))
+            b.step(1)
+            for s, c in zip(systems, cents):
+                qhp.lib().qhp_get_centroid(s.h, c.ctypes.data_as(qhp._DP))
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if rank == 0:
+            out["e2e"] = {"value": units_step * n * ws / dt, "unit": UNIT,
+                          "h2d_bytes_per_step": int(sum(p.numel() * 8 for p in pins)),
+                          "d2h_bytes_per_step": int(sum(c.nbytes for c in cents))}
+    b.close()
+    for s in systems:
+        s.close()
+    if rank == 0 and args.cpu_baseline:
+        rng = np.random.default_rng(7)
+        picks = sorted(rng.choice(len(cfgs), 8, replace=False))
+        t_tot = u_tot = 0.0
+        for k in picks:
+            t, u, *_ = _oracle_sample(cfgs[k], min(2, cfgs[k].P))
+            t_tot += t
+            u_tot += u
+        out["cpu_baseline"] = {"value": u_tot / t_tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"FP64 oracle on 8 of the 256 boxes (indices {list(map(int, picks))}): "
+                                         "forces of 2 beads each + one BAOAB update, numpy, 1 thread"}
+    return out
+
+
 def _e2e(args, h, N, P, step, dev, ws):
     """Public API with host buffers: per step upload the momenta (pinned), step, read back the centroids."""
     import torch
@@ -355,20 +481,33 @@ def run_reference(args, ws, rank, local):
     """Reference arm: the FP64 CPU oracle; each timed step is a one-bead sample of the workload."""
     if rank != 0:
         return None
-    cfg = _config(args.workload)
     k = max(1, args.steps)
     t_tot, units = 0.0, 0
-    for _ in range(k):
-        t, u, *_ = _oracle_sample(cfg, 1)
-        t_tot += t
-        units += u
+    if args.workload == "batch_256":
+        from paper_2212_03137_b300.workloads import batch_configs
+        cfgs = batch_configs()
+        picks = [int(x) for x in np.random.default_rng(7).choice(len(cfgs), 8, replace=False)]
+        for it in range(k):
+            t, u, *_ = _oracle_sample(cfgs[picks[it % 8]], 1)
+            t_tot += t
+            units += u
+        cfg = cfgs[picks[0]]
+        sample = f"FP64 oracle: one box per step from 8 of the 256 boxes {picks}, forces of 1 bead + one BAOAB update"
+        conf = {"workload": "batch_256", "n_systems": len(cfgs), "l2": "n/a (host CPU)", "parallelism": "single process"}
+    else:
+        cfg = _config(args.workload)
+        for _ in range(k):
+            t, u, *_ = _oracle_sample(cfg, 1)
+            t_tot += t
+            units += u
+        sample = f"FP64 oracle: forces of 1 of {cfg.P} beads + one BAOAB update of all modes scaled by 1/{cfg.P}"
+        conf = {"workload": args.workload, "n_atoms": 3 * cfg.n_mol, "beads": cfg.P, "l2": "n/a (host CPU)",
+                "parallelism": "single process"}
     value = units / t_tot
-    sample = f"FP64 oracle: forces of 1 of {cfg.P} beads + one BAOAB update of all modes scaled by 1/{cfg.P}"
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": k, "warmup": args.warmup,
             "ms_per_step": t_tot / k * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "n_atoms": 3 * cfg.n_mol, "beads": cfg.P,
-                       "l2": "n/a (host CPU)", "parallelism": "single process"},
+            "config": conf,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -413,7 +552,12 @@ def main():
         if backend == "nccl":
             torch.cuda.set_device(local)
         td.init_process_group(backend=backend)
-    out = run_ours(args, ws, rank, local) if args.impl == "ours" else run_reference(args, ws, rank, local)
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank, local)
+    elif args.workload == "batch_256":
+        out = run_batch(args, ws, rank, local)
+    else:
+        out = run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as td
         td.destroy_process_group()

@@ -215,6 +215,45 @@ int qhp_energy_grad(qhp_sys sys, double* energy, double* dE_dx, double* dE_dthet
 int qhp_energy_grad_device(qhp_sys sys, const double* x, double* energy, double* dE_dx, double* dE_dtheta);
 int qhp_segment_grad(qhp_sys sys, int K, int block, int observable, double* J, double* dJ_dtheta);
 
+/* Batched systems (the paper's bead parallelism extended to many independent systems;
+ * no counterpart in the paper).  A batch steps n_sys initialised mixed-precision systems
+ * with the PILE or NVE thermostat together: each step is one CUDA graph of batched
+ * launches (integrate, list check, pair - one launch per bead count present -, bonded,
+ * projection; persistent grids over (system, block) work items) plus one conditional
+ * rebuild chain per system that runs only when that system's list check fires.  Results equal stepping every system alone
+ * with the same warps-per-atom setting.  The systems stay owned by the caller and must
+ * outlive the batch; while batched, their work runs on the batch's stream (member calls
+ * such as qhp_get_modes stay valid and ordered), and qhp_set_stream must not be called
+ * on them.  qhp_batch_step is asynchronous; qhp_batch_sync waits and reports the first
+ * member fault.
+ *
+ * qhp_autotune: time the pair kernel of one system with 1, 2 and 4 warps per atom and
+ * keep the fastest (*warps_per_atom receives it; forces are recomputed with it).
+ * qhp_batch_autotune: the same once per bead count present (on its largest member),
+ * applied to every member with that bead count; tuned[7] receives W for P = 1, 2, 4,
+ * ..., 64 (0 where absent; may be NULL). */
+typedef struct qhp_batch_s* qhp_batch;
+typedef struct {
+    int n_sys, kernels_per_step;
+    int64_t atom_beads, steps, rebuilds, kernel_launches;
+    int grid_integrate, grid_pair, grid_bonded, grid_project;
+    int items_pair, reserved;
+} qhp_batch_info;
+int qhp_create_batch(qhp_batch* out, int n_sys, const qhp_sys* systems);
+int qhp_destroy_batch(qhp_batch batch);
+int qhp_batch_step(qhp_batch batch, int n);
+int qhp_batch_sync(qhp_batch batch);
+int qhp_batch_set_stream(qhp_batch batch, void* stream);
+int qhp_batch_autotune(qhp_batch batch, int reps, int* tuned);
+int qhp_batch_get_info(qhp_batch batch, qhp_batch_info* out);
+/* Stage durations of the last batched step (ms), as qhp_get_profile: integrate, list
+ * check + rebuild bodies, pair, bonded, projection.  Synchronises the batch's stream. */
+int qhp_batch_get_profile(qhp_batch batch, qhp_profile* out);
+int qhp_autotune(qhp_sys sys, int reps, int* warps_per_atom);
+/* Fix the warps per atom of the mixed pair kernel (1, 2 or 4; 0 = the default for P:
+ * 4 if P >= 16, else 1).  Different settings sum the pair forces in different orders. */
+int qhp_set_pair_warps(qhp_sys sys, int warps_per_atom);
+
 /* Launch mode of qhp_step_rpmd / qhp_step_adqtb.  use_graphs = 1 (default): each
  * step replays one captured CUDA graph whose list-rebuild chain sits behind a
  * conditional node.  use_graphs = 0: the same kernels are launched one by one and

@@ -77,8 +77,9 @@ def neighbours_of(i: int, C: np.ndarray, mol: np.ndarray, L: float, r_list: floa
 
 
 def use_centroid_list(L: float, rc: float, skin: float) -> bool:
-    """Reading for small boxes: the centroid list is used only when the cell grid is at
-    least 5 wide (125 distinct stencil cells) and r_list < L/2; otherwise every pair of
-    different molecules is visited with a per-bead minimum image."""
+    """Reading for small boxes: the cell grid is used only when it is at least 5 wide
+    (125 distinct stencil cells) and r_list < L/2.  Otherwise the same list (pairs of
+    different molecules with minimum-image centroid distance below r_list) is found by
+    brute force, and the pair sum applies a per-bead minimum image."""
     r_list = rc + skin
     return cell_grid(L, r_list) >= 5 and r_list < 0.5 * L

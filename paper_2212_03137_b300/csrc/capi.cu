@@ -255,7 +255,8 @@ int enqueue_segment_end(qhp_system_s* s, int64_t steps_done) {
 int ensure_capacity(qhp_system_s* s) {
     int64_t longest = 0;
     TRY(host_list_size(s, &longest));
-    int64_t row = s->list_mode ? ((int64_t)(1.25 * (double)longest) + 64 + 7) / 8 * 8 : (int64_t)s->N;
+    int64_t row = ((int64_t)(1.25 * (double)longest) + 64 + 7) / 8 * 8;
+    if (row > s->N) row = s->N;   // no row is longer than the other atoms
     if (row < 8) row = 8;
     if (row * (int64_t)s->N > ((int64_t)1 << 31) - 1) {
         qhp::set_error("neighbour list too large (%lld rows of %lld entries)", (long long)s->N, (long long)row);
@@ -350,6 +351,9 @@ double self_energy(const qhp_system_s* s) {
 }
 
 }  // namespace
+
+void graph_invalidate(qhp_system_s* s) { invalidate_graph(s); }
+int system_sync(qhp_system_s* s) { return sync_and_check(s); }
 
 // Rebuild the list around the current modes now (synchronous).  The rebuild chain checks
 // that every bead lies within skin/2 of its anchor and reports QHP_ERR_LIST_OVERFLOW if not.

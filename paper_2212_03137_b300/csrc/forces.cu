@@ -19,6 +19,9 @@
 // FP64 forces.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "qhp_internal.cuh"
 
 namespace qhp {
@@ -107,33 +110,53 @@ __device__ __forceinline__ void pair_term(float dx, float dy, float dz, float qq
 }
 
 constexpr int PAIR_WARPS = 4;   // warps per block
+constexpr int PAIR_RED = PAIR_WARPS * 4 * 64;   // floats of the cross-warp reduction buffer
 
-// Warps that share one atom's list: with many beads (P >= 16) four warps split the list;
-// with few beads one warp takes a whole list (32/P entries per iteration) and a block
-// holds four atoms.
-template <int P>
-__host__ __device__ constexpr int pair_warps_per_atom() { return P >= 16 ? 4 : 1; }
+// Warps that share one atom's list (W): with many beads (P >= 16) four warps split the
+// list; with few beads one warp takes a whole list (32/P entries per iteration) and a
+// block holds four atoms.  This is the default; the autotuner may pick another W.
+__host__ __device__ constexpr int pair_warps_default(int P) { return P >= 16 ? 4 : 1; }
 
-template <int P, bool ALL, bool ENERGY>
-__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const float4* __restrict__ pos, const int* __restrict__ start, const int* __restrict__ count,
-                                                    const int4* __restrict__ nbr, const float* __restrict__ charge_s,
-                                                    const int* __restrict__ type_s, const int* __restrict__ perm,
-                                                    long long* __restrict__ F, float* __restrict__ epair, PairConsts c,
-                                                    const unsigned* __restrict__ status) {
+struct PairArgs {
+    int N, P, W, all;
+    const float4* pos;
+    const int *start, *count;
+    const int4* nbr;
+    const float* charge_s;
+    const int *type_s, *perm;
+    long long* F;
+    float* epair;
+    const unsigned* status;
+    PairConsts c;
+};
+
+// One block (bx) of the pair kernel: APB = PAIR_WARPS / W atoms.  red: PAIR_RED floats.
+template <int P, int W, bool ALL, bool ENERGY>
+__device__ __forceinline__ void pair_body(const PairArgs& A, int bx, float* red_raw) {
     constexpr int JPW = P >= 32 ? 1 : 32 / P;
     constexpr int BPL = P > 32 ? P / 32 : 1;
     constexpr int NB = P > 32 ? P : 32;                   // bead slots reduced across warps
-    constexpr int W = pair_warps_per_atom<P>();
     constexpr int APB = PAIR_WARPS / W;                   // atoms per block
-    __shared__ float red[PAIR_WARPS][4][NB];
+    float(*red)[4][NB] = reinterpret_cast<float(*)[4][NB]>(red_raw);
+    const int N = A.N;
+    const float4* __restrict__ pos = A.pos;
+    const int* __restrict__ start = A.start;
+    const int* __restrict__ count = A.count;
+    const int4* __restrict__ nbr = A.nbr;
+    const float* __restrict__ charge_s = A.charge_s;
+    const int* __restrict__ type_s = A.type_s;
+    const int* __restrict__ perm = A.perm;
+    long long* __restrict__ F = A.F;
+    float* __restrict__ epair = A.epair;
+    const PairConsts& c = A.c;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int wa = w % W;                                 // this warp's chunk of the atom's list
-    const int i_raw = blockIdx.x * APB + w / W;
+    const int i_raw = bx * APB + w / W;
     const bool live = i_raw < N;
     const int i = live ? i_raw : N - 1;                   // idle warps still reach the barrier
     const int b0 = P >= 32 ? lane : (lane % P);
     const int jsub = P >= 32 ? 0 : lane / P;
-    const bool ok = live && (*status & ST_LIST_OVERFLOW) == 0u;
+    const bool ok = live && (*A.status & ST_LIST_OVERFLOW) == 0u;
     // N * P < 2^30 is checked at set-up, so 32-bit element offsets suffice
     const float4* __restrict__ pl = pos + b0;
 
@@ -226,6 +249,37 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(int N, const flo
     }
 }
 
+template <int P, int W, bool ALL, bool ENERGY>
+__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(const __grid_constant__ PairArgs A) {
+    __shared__ float red[PAIR_RED];
+    pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, red);
+}
+
+// Batched systems: one persistent launch per bead count, over the (system, block) items of
+// the systems with that P; each item's warps per atom and list mode select the
+// specialisation (uniform over the block).  One launch per P keeps every launch at the
+// registers of its own bead count.
+template <int P>
+__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_batch(const PairArgs* __restrict__ args,
+                                                                const int2* __restrict__ items,
+                                                                const int* __restrict__ ranges) {
+    __shared__ float red[PAIR_RED];
+    for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
+        const int2 w = items[it];
+        const PairArgs& A = args[w.x];
+        __syncthreads();   // the previous item's reduction has been read
+        if (A.all) {
+            if (A.W == 4) pair_body<P, 4, true, false>(A, w.y, red);
+            else if (A.W == 2) pair_body<P, 2, true, false>(A, w.y, red);
+            else pair_body<P, 1, true, false>(A, w.y, red);
+        } else {
+            if (A.W == 4) pair_body<P, 4, false, false>(A, w.y, red);
+            else if (A.W == 2) pair_body<P, 2, false, false>(A, w.y, red);
+            else pair_body<P, 1, false, false>(A, w.y, red);
+        }
+    }
+}
+
 template <bool ENERGY>
 __global__ void __launch_bounds__(128) k_pair_fp64(int N, int P, const double* __restrict__ pos,
                                                    const int* __restrict__ start, const int* __restrict__ count,
@@ -308,11 +362,29 @@ struct BondConsts {
 };
 
 // Bonded terms per (molecule, bead); each thread owns the forces of its three atoms at its bead.
+struct BondArgs {
+    int n_mol, N, P;
+    const float4* pos_f;
+    const double* pos_d;
+    const float* dA;
+    const int* iperm;
+    long long* Ffix;
+    double* Fd;
+    double* ebond;
+    BondConsts c;
+};
+
 template <bool MIXED, bool ENERGY>
-__global__ void k_bonded(int n_mol, int N, int P, const float4* __restrict__ pos_f, const double* __restrict__ pos_d,
-                         const float* __restrict__ dA, const int* __restrict__ iperm, long long* Ffix, double* Fd,
-                         double* ebond, BondConsts c) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bonded_body(const BondArgs& A, int t) {
+    const int n_mol = A.n_mol, N = A.N, P = A.P;
+    const float4* __restrict__ pos_f = A.pos_f;
+    const double* __restrict__ pos_d = A.pos_d;
+    const float* __restrict__ dA = A.dA;
+    const int* __restrict__ iperm = A.iperm;
+    long long* Ffix = A.Ffix;
+    double* Fd = A.Fd;
+    double* ebond = A.ebond;
+    const BondConsts& c = A.c;
     if (t >= n_mol * P) return;
     const int m = t / P, b = t % P;
     const int aO = 3 * m, aH1 = aO + 1, aH2 = aO + 2;
@@ -377,6 +449,19 @@ __global__ void k_bonded(int n_mol, int N, int P, const float4* __restrict__ pos
         if (ENERGY)
             ebond[t] = 0.5 * c.kb * ((r1 - c.r0) * (r1 - c.r0) + (r2 - c.r0) * (r2 - c.r0)) +
                        0.5 * c.kth * (th - c.th0) * (th - c.th0);
+    }
+}
+
+template <bool MIXED, bool ENERGY>
+__global__ void k_bonded(const __grid_constant__ BondArgs A) {
+    bonded_body<MIXED, ENERGY>(A, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_bonded_batch(const BondArgs* __restrict__ args, const int2* __restrict__ items,
+                               const int* __restrict__ ranges) {
+    for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
+        const int2 w = items[it];
+        bonded_body<true, false>(args[w.x], w.y * (int)blockDim.x + threadIdx.x);
     }
 }
 
@@ -466,29 +551,59 @@ PairConsts make_pair_consts(const qhp_system_s* s) {
     return c;
 }
 
-template <int P>
-void pair_mixed_dispatch(qhp_system_s* s, bool energy, const PairConsts& c, int /*unused*/) {
-    constexpr int apb = PAIR_WARPS / pair_warps_per_atom<P>();
-    const int grid = (s->N + apb - 1) / apb;
-    if (s->list_mode) {
-        if (energy)
-            k_pair_mixed<P, false, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
-                                                                      s->type_s, s->perm, s->Ffix, s->e_pair, c,
-                                                                      s->status);
-        else
-            k_pair_mixed<P, false, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr,
-                                                                       s->charge_s, s->type_s, s->perm, s->Ffix,
-                                                                       s->e_pair, c, s->status);
+PairArgs make_pair_args(const qhp_system_s* s) {
+    PairArgs A;
+    A.N = s->N;
+    A.P = s->P;
+    A.W = s->pair_w > 0 ? s->pair_w : pair_warps_default(s->P);
+    A.all = s->list_mode ? 0 : 1;
+    A.pos = s->pos_f4;
+    A.start = s->nbr_start;
+    A.count = s->nbr_count;
+    A.nbr = s->nbr;
+    A.charge_s = s->charge_s;
+    A.type_s = s->type_s;
+    A.perm = s->perm;
+    A.F = s->Ffix;
+    A.epair = s->e_pair;
+    A.status = s->status;
+    A.c = make_pair_consts(s);
+    return A;
+}
+
+template <int P, int W>
+void pair_mixed_launch(const PairArgs& A, bool energy, cudaStream_t st) {
+    const int grid = (A.N + PAIR_WARPS / W - 1) / (PAIR_WARPS / W);
+    if (A.all) {
+        if (energy) k_pair_mixed<P, W, true, true><<<grid, 32 * PAIR_WARPS, 0, st>>>(A);
+        else k_pair_mixed<P, W, true, false><<<grid, 32 * PAIR_WARPS, 0, st>>>(A);
     } else {
-        if (energy)
-            k_pair_mixed<P, true, true><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
-                                                                     s->type_s, s->perm, s->Ffix, s->e_pair, c,
-                                                                     s->status);
-        else
-            k_pair_mixed<P, true, false><<<grid, 32 * PAIR_WARPS, 0, s->stream>>>(s->N, s->pos_f4, s->nbr_start, s->nbr_count, s->nbr,
-                                                                      s->charge_s, s->type_s, s->perm, s->Ffix,
-                                                                      s->e_pair, c, s->status);
+        if (energy) k_pair_mixed<P, W, false, true><<<grid, 32 * PAIR_WARPS, 0, st>>>(A);
+        else k_pair_mixed<P, W, false, false><<<grid, 32 * PAIR_WARPS, 0, st>>>(A);
     }
+}
+
+template <int P>
+void pair_mixed_dispatch(const PairArgs& A, bool energy, cudaStream_t st) {
+    if (A.W == 4) pair_mixed_launch<P, 4>(A, energy, st);
+    else if (A.W == 2) pair_mixed_launch<P, 2>(A, energy, st);
+    else pair_mixed_launch<P, 1>(A, energy, st);
+}
+
+BondArgs make_bond_args(const qhp_system_s* s) {
+    BondArgs B;
+    B.n_mol = s->n_mol;
+    B.N = s->N;
+    B.P = s->P;
+    B.pos_f = s->pos_f4;
+    B.pos_d = s->pos_d;
+    B.dA = s->dA;
+    B.iperm = s->iperm;
+    B.Ffix = s->Ffix;
+    B.Fd = s->Fd;
+    B.ebond = s->e_bond;
+    B.c = BondConsts{s->ff.k_b, s->ff.r0, s->ff.k_theta, s->ff.theta0, s->L};
+    return B;
 }
 
 }  // namespace
@@ -496,16 +611,16 @@ void pair_mixed_dispatch(qhp_system_s* s, bool energy, const PairConsts& c, int 
 cudaError_t launch_pair(qhp_system_s* s, bool energy) {
     const PairConsts c = make_pair_consts(s);
     const int grid = (s->N * 32 + 127) / 128;
-    const int gm = s->N;   // mixed: one block per sorted atom
     if (s->precision == QHP_MIXED) {
+        const PairArgs A = make_pair_args(s);
         switch (s->P) {
-            case 1: pair_mixed_dispatch<1>(s, energy, c, gm); break;
-            case 2: pair_mixed_dispatch<2>(s, energy, c, gm); break;
-            case 4: pair_mixed_dispatch<4>(s, energy, c, gm); break;
-            case 8: pair_mixed_dispatch<8>(s, energy, c, gm); break;
-            case 16: pair_mixed_dispatch<16>(s, energy, c, gm); break;
-            case 32: pair_mixed_dispatch<32>(s, energy, c, gm); break;
-            case 64: pair_mixed_dispatch<64>(s, energy, c, gm); break;
+            case 1: pair_mixed_dispatch<1>(A, energy, s->stream); break;
+            case 2: pair_mixed_dispatch<2>(A, energy, s->stream); break;
+            case 4: pair_mixed_dispatch<4>(A, energy, s->stream); break;
+            case 8: pair_mixed_dispatch<8>(A, energy, s->stream); break;
+            case 16: pair_mixed_dispatch<16>(A, energy, s->stream); break;
+            case 32: pair_mixed_dispatch<32>(A, energy, s->stream); break;
+            case 64: pair_mixed_dispatch<64>(A, energy, s->stream); break;
             default: return cudaErrorInvalidValue;
         }
     } else {
@@ -523,18 +638,111 @@ cudaError_t launch_pair(qhp_system_s* s, bool energy) {
 }
 
 cudaError_t launch_bonded(qhp_system_s* s, bool energy) {
-    BondConsts bc{s->ff.k_b, s->ff.r0, s->ff.k_theta, s->ff.theta0, s->L};
-    const int nt = s->n_mol * s->P;
-    const int g2 = (nt + 127) / 128;
-    const bool mixed = s->precision == QHP_MIXED;
-    if (mixed) {
-        if (energy) k_bonded<true, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
-        else k_bonded<true, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+    const BondArgs B = make_bond_args(s);
+    const int g2 = (s->n_mol * s->P + 127) / 128;
+    if (s->precision == QHP_MIXED) {
+        if (energy) k_bonded<true, true><<<g2, 128, 0, s->stream>>>(B);
+        else k_bonded<true, false><<<g2, 128, 0, s->stream>>>(B);
     } else {
-        if (energy) k_bonded<false, true><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
-        else k_bonded<false, false><<<g2, 128, 0, s->stream>>>(s->n_mol, s->N, s->P, s->pos_f4, s->pos_d, s->dA, s->iperm, s->Ffix, s->Fd, s->e_bond, bc);
+        if (energy) k_bonded<false, true><<<g2, 128, 0, s->stream>>>(B);
+        else k_bonded<false, false><<<g2, 128, 0, s->stream>>>(B);
     }
     s->launches += 1;
+    return cudaGetLastError();
+}
+
+// Batched stages (mixed precision).  Pair items are blocks of PAIR_WARPS / W atoms, costed
+// by the bead-pair work of their list rows (row length x max(P, 32) lanes); one stage per
+// bead count (stage index log2 P).
+template <int P>
+const void* pair_batch_kernel() { return (const void*)k_pair_batch<P>; }
+
+const void* pair_batch_kernel_for(int P) {
+    switch (P) {
+        case 1: return pair_batch_kernel<1>();
+        case 2: return pair_batch_kernel<2>();
+        case 4: return pair_batch_kernel<4>();
+        case 8: return pair_batch_kernel<8>();
+        case 16: return pair_batch_kernel<16>();
+        case 32: return pair_batch_kernel<32>();
+        default: return pair_batch_kernel<64>();
+    }
+}
+
+int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[7]*/) {
+    for (int lp = 0; lp < 7; ++lp) {
+        const int P = 1 << lp;
+        std::vector<PairArgs> a;
+        std::vector<int2> items;
+        std::vector<double> cost;
+        for (size_t k = 0; k < v.size(); ++k) {
+            const qhp_system_s* s = v[k];
+            if (s->P != P) continue;
+            const int idx = (int)a.size();
+            a.push_back(make_pair_args(s));
+            const int apb = PAIR_WARPS / a.back().W;
+            const int nb = (s->N + apb - 1) / apb;
+            std::vector<int> cnt(s->N);
+            QHP_CUDA(cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * s->N, cudaMemcpyDeviceToHost));
+            const double lanes = (double)std::max(P, 32) / 32.0;
+            for (int b = 0; b < nb; ++b) {
+                double c = 0.0;
+                for (int i = b * apb; i < std::min(s->N, (b + 1) * apb); ++i) c += (double)cnt[i] * lanes;
+                items.push_back(make_int2(idx, b));
+                cost.push_back(c + 8.0);
+            }
+        }
+        if (a.empty()) {
+            stage_free(st[lp]);
+            continue;
+        }
+        int per_sm = 0;
+        QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_batch_kernel_for(P), 32 * PAIR_WARPS, 0));
+        st[lp].smem = 0;
+        TRY(stage_upload(st[lp], a.data(), sizeof(PairArgs) * a.size(), items, cost, std::max(1, per_sm) * sm_count()));
+    }
+    return QHP_OK;
+}
+
+int batch_stage_bonded(const std::vector<qhp_system_s*>& v, BatchStage& st) {
+    std::vector<BondArgs> a;
+    std::vector<int2> items;
+    std::vector<double> cost;
+    for (size_t k = 0; k < v.size(); ++k) {
+        a.push_back(make_bond_args(v[k]));
+        const int nb = (v[k]->n_mol * v[k]->P + 127) / 128;
+        for (int b = 0; b < nb; ++b) {
+            items.push_back(make_int2((int)k, b));
+            cost.push_back(1.0);
+        }
+    }
+    int per_sm = 0;
+    QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bonded_batch, 128, 0));
+    st.smem = 0;
+    return stage_upload(st, a.data(), sizeof(BondArgs) * a.size(), items, cost, std::max(1, per_sm) * sm_count());
+}
+
+cudaError_t launch_batch_pair(const BatchStage* st, cudaStream_t stream) {
+    for (int lp = 0; lp < 7; ++lp) {
+        if (st[lp].n_items == 0) continue;
+        const PairArgs* a = (const PairArgs*)st[lp].args;
+        switch (lp) {
+            case 0: k_pair_batch<1><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
+            case 1: k_pair_batch<2><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
+            case 2: k_pair_batch<4><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
+            case 3: k_pair_batch<8><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
+            case 4: k_pair_batch<16><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
+            case 5: k_pair_batch<32><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
+            default: k_pair_batch<64><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch_bonded(const BatchStage& st, cudaStream_t stream) {
+    k_bonded_batch<<<st.grid, 128, 0, stream>>>((const BondArgs*)st.args, st.items, st.ranges);
     return cudaGetLastError();
 }
 

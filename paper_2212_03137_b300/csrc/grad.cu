@@ -466,13 +466,9 @@ cudaError_t eval_terms(qhp_system_s* s, int Pk, bool dual, const double* x, cons
     return cudaGetLastError();
 }
 
-// The list must cover the configuration about to be evaluated.  All-pairs rows never
-// change; a centroid list is rebuilt around the current modes.
-int ensure_list_for_current_modes(qhp_system_s* s) {
-    if (s->list_mode) return rebuild_list_now(s);
-    if (!s->list_valid) TRY(qhp_build_list(s));
-    return QHP_OK;
-}
+// The list must cover the configuration about to be evaluated: it is rebuilt around the
+// current modes (the rows depend on the centroids in both list modes).
+int ensure_list_for_current_modes(qhp_system_s* s) { return rebuild_list_now(s); }
 
 // Hessian-vector product at the modes Qk along lamP with weight w:
 //   lamQ += w (df/dQ)^T lamP,  acc[1..5] += w (df/dtheta)^T lamP.
@@ -647,7 +643,7 @@ int qhp_segment_grad(qhp_sys s, int K, int block, int observable, double* J, dou
         // backwards through the block
         for (int k = k1; k > k0 && rc == QHP_OK; --k) {
             const double* Qk = g.Qbuf + (size_t)(k - k0) * NP3;
-            if (s->list_mode) rc = load_modes(s, Qk);
+            rc = load_modes(s, Qk);
             if (rc == QHP_OK) rc = observe(s, Qk, observable, wK, scoef);
             if (rc == QHP_OK && k < K) rc = hvp(s, Qk, 2.0 * h);
             if (rc == QHP_OK) {
@@ -660,7 +656,7 @@ int qhp_segment_grad(qhp_sys s, int K, int block, int observable, double* J, dou
         }
         // start of the segment: only the theta part of the first kick matters
         if (c == 0 && rc == QHP_OK) {
-            if (s->list_mode) rc = load_modes(s, g.Qbuf);
+            rc = load_modes(s, g.Qbuf);
             if (rc == QHP_OK) rc = hvp(s, g.Qbuf, h);
         }
     }

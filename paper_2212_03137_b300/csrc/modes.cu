@@ -7,6 +7,8 @@
 // so the P x P bead transform of an atom happens in shared memory.
 #include <math.h>
 
+#include <algorithm>
+
 #include "qhp_internal.cuh"
 
 namespace qhp {
@@ -62,10 +64,11 @@ __device__ __forceinline__ void free_half(int n, const double* c, double& q, dou
 
 // B(dt/2) A(dt/2) O(dt) A(dt/2) on each mode (Eq. (17)), then x = sqrt(P) T Q (Eq. (4)).
 // INTEGRATE = false only recomputes bead positions (after a list rebuild or set_modes).
+// One block of atoms (bx-th group of apb atoms); load_T = false keeps the transposed
+// transform already staged in shared memory by the previous block of the same system.
 template <bool MIXED, bool ADQTB, bool INTEGRATE>
-__global__ void __launch_bounds__(BLOCK) k_integrate(IntegrateArgs A) {
-    extern __shared__ unsigned char smem_raw[];
-    if (A.gate && !*A.gate) return;                                   // uniform over the grid
+__device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, unsigned char* smem_raw,
+                                               bool load_T) {
     const int P = A.P;
     double* qs = reinterpret_cast<double*>(smem_raw);                 // [BLOCK]
     float* qf = reinterpret_cast<float*>(qs + BLOCK);                 // [BLOCK]
@@ -75,16 +78,17 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(IntegrateArgs A) {
 
     const int t = threadIdx.x;
     const int la = t / (3 * P), d = (t / P) % 3, n = t % P;
-    const int a = blockIdx.x * A.apb + la;
+    const int a = bx * A.apb + la;
     const bool valid = a < A.N;
     const int idx = (a * 3 + d) * P + n;
 
     // transpose to [mode k][bead b] so that the lanes (beads) of a warp read consecutive words
-    for (int e = t; e < P * P; e += BLOCK) {
-        const int b = e / P, k = e % P;
-        if (MIXED) Tsf[k * P + b] = A.Tmf[e];
-        else Tsd[k * P + b] = A.Tm[e];
-    }
+    if (load_T)
+        for (int e = t; e < P * P; e += BLOCK) {
+            const int b = e / P, k = e % P;
+            if (MIXED) Tsf[k * P + b] = A.Tmf[e];
+            else Tsd[k * P + b] = A.Tm[e];
+        }
 
     double q = 0.0, pm = 0.0;
     if (valid) {
@@ -148,6 +152,28 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(IntegrateArgs A) {
     block_max_atomic(dv, A.dev_max);
 }
 
+template <bool MIXED, bool ADQTB, bool INTEGRATE>
+__global__ void __launch_bounds__(BLOCK) k_integrate(const __grid_constant__ IntegrateArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    if (A.gate && !*A.gate) return;                                   // uniform over the grid
+    integrate_body<MIXED, ADQTB, INTEGRATE>(A, blockIdx.x, smem_raw, true);
+}
+
+// Batched systems: a persistent grid, each block walking its contiguous range of
+// (system, atom-group) items; the transform is restaged only when the system changes.
+__global__ void __launch_bounds__(BLOCK) k_integrate_batch(const IntegrateArgs* __restrict__ args,
+                                                           const int2* __restrict__ items,
+                                                           const int* __restrict__ ranges) {
+    extern __shared__ unsigned char smem_raw[];
+    int prev = -1;
+    for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
+        const int2 w = items[it];
+        __syncthreads();   // the previous item is done with shared memory
+        integrate_body<true, false, true>(args[w.x], w.y, smem_raw, w.x != prev);
+        prev = w.x;
+    }
+}
+
 struct ProjectArgs {
     int N, P, apb;
     double half_dt_acc;
@@ -163,23 +189,23 @@ struct ProjectArgs {
 
 // f_n = (1/sqrt P) sum_b T_bn F_b (Eqs. (10)-(11)) and, with KICK, B(dt/2) P_n += dt/2 f_n.
 template <bool MIXED, bool KICK>
-__global__ void __launch_bounds__(BLOCK) k_project(ProjectArgs A) {
+__device__ __forceinline__ void project_body(const ProjectArgs& A, int bx, unsigned char* smem_raw, bool load_T) {
     __shared__ double Fs[BLOCK];
     __shared__ long long Fi[BLOCK];
     __shared__ float Ff[BLOCK];
-    extern __shared__ unsigned char smem_raw[];
     const int P = A.P;
     float* Tsf = reinterpret_cast<float*>(smem_raw);
     double* Tsd = reinterpret_cast<double*>(smem_raw);
     const int t = threadIdx.x;
     const int la = t / (3 * P), d = (t / P) % 3, n = t % P;
-    const int a = blockIdx.x * A.apb + la;
+    const int a = bx * A.apb + la;
     const bool valid = a < A.N;
     const int idx = (a * 3 + d) * P + n;
-    for (int k = t; k < P * P; k += BLOCK) {
-        if (MIXED) Tsf[k] = A.Tpf[k];
-        else Tsd[k] = A.Tp[k];
-    }
+    if (load_T)
+        for (int k = t; k < P * P; k += BLOCK) {
+            if (MIXED) Tsf[k] = A.Tpf[k];
+            else Tsd[k] = A.Tp[k];
+        }
     if (valid) {
         if (MIXED) {
             const long long v = A.Ffix[idx];
@@ -215,7 +241,26 @@ __global__ void __launch_bounds__(BLOCK) k_project(ProjectArgs A) {
             if (!isfinite(p)) atomicOr(A.status, ST_NONFINITE);
         }
     }
-    if (KICK && blockIdx.x == 0 && t == 0) *A.step_ctr += 1ull;
+    if (KICK && bx == 0 && t == 0) *A.step_ctr += 1ull;
+}
+
+template <bool MIXED, bool KICK>
+__global__ void __launch_bounds__(BLOCK) k_project(const __grid_constant__ ProjectArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    project_body<MIXED, KICK>(A, blockIdx.x, smem_raw, true);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_project_batch(const ProjectArgs* __restrict__ args,
+                                                         const int2* __restrict__ items,
+                                                         const int* __restrict__ ranges) {
+    extern __shared__ unsigned char smem_raw[];
+    int prev = -1;
+    for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
+        const int2 w = items[it];
+        __syncthreads();
+        project_body<true, true>(args[w.x], w.y, smem_raw, w.x != prev);
+        prev = w.x;
+    }
 }
 
 __global__ void k_init_modes(int N, int P, uint64_t seed, double kT_acc, const double* pos0, const double* mass,
@@ -395,7 +440,7 @@ cudaError_t launch_integrate(qhp_system_s* s, bool integrate, bool adqtb) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(qhp_system_s* s, bool kick) {
+static ProjectArgs make_pargs(qhp_system_s* s) {
     ProjectArgs A;
     A.N = s->N;
     A.P = s->P;
@@ -409,6 +454,11 @@ cudaError_t launch_project(qhp_system_s* s, bool kick) {
     A.Pm = s->Pm;
     A.status = s->status;
     A.step_ctr = s->step_ctr;
+    return A;
+}
+
+cudaError_t launch_project(qhp_system_s* s, bool kick) {
+    const ProjectArgs A = make_pargs(s);
     const int grid = (s->N + A.apb - 1) / A.apb;
     const bool mixed = s->precision == QHP_MIXED;
     const size_t sm = (size_t)s->P * s->P * (mixed ? 4 : 8);
@@ -420,6 +470,48 @@ cudaError_t launch_project(qhp_system_s* s, bool kick) {
         if (kick) k_project<false, true><<<grid, BLOCK, sm, s->stream>>>(A);
         else k_project<false, false><<<grid, BLOCK, sm, s->stream>>>(A);
     }
+    return cudaGetLastError();
+}
+
+// Batched stages (mixed precision, PILE/NVE): one item per block of 64/P atoms.
+template <class Args, class Make>
+static int integrate_like_stage(const std::vector<qhp_system_s*>& v, BatchStage& st, Make make, const void* kernel,
+                                size_t smem_per_P_sq) {
+    std::vector<Args> a;
+    std::vector<int2> items;
+    std::vector<double> cost;
+    int maxP = 1;
+    for (size_t k = 0; k < v.size(); ++k) {
+        a.push_back(make(v[k]));
+        const int apb = 64 / v[k]->P;
+        const int nb = (v[k]->N + apb - 1) / apb;
+        for (int b = 0; b < nb; ++b) {
+            items.push_back(make_int2((int)k, b));
+            cost.push_back(1.0);
+        }
+        maxP = std::max(maxP, v[k]->P);
+    }
+    st.smem = smem_per_P_sq * maxP * maxP + (kernel == (const void*)k_integrate_batch ? BLOCK * 16 : 0);
+    int per_sm = 0;
+    QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BLOCK, st.smem));
+    return stage_upload(st, a.data(), sizeof(Args) * a.size(), items, cost, std::max(1, per_sm) * sm_count());
+}
+
+int batch_stage_integrate(const std::vector<qhp_system_s*>& v, BatchStage& st) {
+    return integrate_like_stage<IntegrateArgs>(v, st, make_iargs, (const void*)k_integrate_batch, 4);
+}
+
+int batch_stage_project(const std::vector<qhp_system_s*>& v, BatchStage& st) {
+    return integrate_like_stage<ProjectArgs>(v, st, make_pargs, (const void*)k_project_batch, 4);
+}
+
+cudaError_t launch_batch_integrate(const BatchStage& st, cudaStream_t stream) {
+    k_integrate_batch<<<st.grid, BLOCK, st.smem, stream>>>((const IntegrateArgs*)st.args, st.items, st.ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_project(const BatchStage& st, cudaStream_t stream) {
+    k_project_batch<<<st.grid, BLOCK, st.smem, stream>>>((const ProjectArgs*)st.args, st.items, st.ranges);
     return cudaGetLastError();
 }
 

@@ -75,6 +75,20 @@ __global__ void k_check(unsigned* dev_max, float thr2, int* flag, int force, uns
     }
 }
 
+__global__ void k_check_batch(const CheckArgs* __restrict__ a, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float dmax = __uint_as_float(*a[k].dev_max);
+    const int rebuild = !(dmax <= a[k].thr2);
+    *a[k].flag = rebuild;
+    if (rebuild) {
+        *a[k].dev_max = 0u;
+        a[k].rebuild_count[0] += 1u;
+        a[k].rebuild_count[1] += 1u;
+    }
+    cudaGraphSetConditional(a[k].cond, rebuild ? 1u : 0u);
+}
+
 // Right after a rebuild the deviation maximum is measured from the new anchors; the list
 // covers every bead pair within rc only if no bead lies farther than skin/2 from its anchor.
 __global__ void k_check_cover(const int* flag, const unsigned* dev_max, float thr2, unsigned* status) {
@@ -208,74 +222,6 @@ __global__ void k_sorted_attrs(const int* flag, int N, double L, const int* perm
         for (int d = 0; d < 3; ++d) out[d] = (float)min_image_rn(anchor[a * 3 + d] - anchor[o * 3 + d], L);
         out[3] = 0.0f;
     }
-}
-
-// Centroid Verlet list, warp per sorted atom i; FILL = false counts, true writes entries.
-template <bool FILL>
-__global__ void k_list(const int* flag, int N, double L, int n_c, double r2max, float lo2, float hi2,
-                       const int* perm, const int* cell, const int* cell_start, const float4* cw, const float4* cwl,
-                       const int* mol_s, const int* type_s, const double* anchor, int* count, const int* start,
-                       int4* nbr, int64_t cap) {
-    if (!*flag) return;
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= N) return;
-    const int ai = perm[i];
-    const int ci = cell[ai];
-    const int cx = ci % n_c, cy = (ci / n_c) % n_c, cz = ci / (n_c * n_c);
-    const float4 wi = cw[i];
-    const float4 li = FILL ? cwl[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float Llo = (float)(L - (double)(float)L);   // L = Lf + Llo
-    const int mi = mol_s[i];
-    const double Ci0 = anchor[ai * 3], Ci1 = anchor[ai * 3 + 1], Ci2 = anchor[ai * 3 + 2];
-    const float Lf = (float)L;
-    int cnt = 0;
-    const int base = FILL ? start[i] : 0;
-    for (int dz = -2; dz <= 2; ++dz)
-        for (int dy = -2; dy <= 2; ++dy)
-            for (int dx = -2; dx <= 2; ++dx) {
-                int x = cx + dx, y = cy + dy, z = cz + dz;
-                float sx = 0.f, sy = 0.f, sz = 0.f;
-                if (x < 0) { x += n_c; sx = -Lf; } else if (x >= n_c) { x -= n_c; sx = Lf; }
-                if (y < 0) { y += n_c; sy = -Lf; } else if (y >= n_c) { y -= n_c; sy = Lf; }
-                if (z < 0) { z += n_c; sz = -Lf; } else if (z >= n_c) { z -= n_c; sz = Lf; }
-                const int cj = (z * n_c + y) * n_c + x;
-                const int j0 = cell_start[cj], j1 = cell_start[cj + 1];
-                for (int jb = j0; jb < j1; jb += 32) {
-                    const int j = jb + lane;
-                    bool acc = false;
-                    if (j < j1 && mol_s[j] != mi) {
-                        const float4 wj = cw[j];
-                        const float ddx = (wj.x + sx) - wi.x, ddy = (wj.y + sy) - wi.y, ddz = (wj.z + sz) - wi.z;
-                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (r2 < lo2) {
-                            acc = true;
-                        } else if (r2 <= hi2) {
-                            const int aj = perm[j];
-                            const double ex = min_image_rn(__dsub_rn(anchor[aj * 3], Ci0), L);
-                            const double ey = min_image_rn(__dsub_rn(anchor[aj * 3 + 1], Ci1), L);
-                            const double ez = min_image_rn(__dsub_rn(anchor[aj * 3 + 2], Ci2), L);
-                            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-                            acc = d2 < r2max;
-                        }
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, acc);
-                    if (FILL && acc) {
-                        const int64_t pos = (int64_t)base + cnt + __popc(bal & ((1u << lane) - 1u));
-                        if (pos < cap) {
-                            // D_ij = (w_j + stencil shift) - w_i from the double-float wrapped anchors
-                            const float4 wj = cw[j], lj = cwl[j];
-                            const float Dx = sep_df(wj.x, lj.x, wi.x, li.x, sx, sx > 0.f ? Llo : (sx < 0.f ? -Llo : 0.f));
-                            const float Dy = sep_df(wj.y, lj.y, wi.y, li.y, sy, sy > 0.f ? Llo : (sy < 0.f ? -Llo : 0.f));
-                            const float Dz = sep_df(wj.z, lj.z, wi.z, li.z, sz, sz > 0.f ? Llo : (sz < 0.f ? -Llo : 0.f));
-                            nbr[pos] = make_int4(j | (type_s[j] ? (int)0x80000000u : 0), __float_as_int(Dx),
-                                                 __float_as_int(Dy), __float_as_int(Dz));
-                        }
-                    }
-                    cnt += __popc(bal);
-                }
-            }
-    if (!FILL && lane == 0) count[i] = cnt;
 }
 
 // Centroid Verlet list, one block per cell: the 125 stencil cells' candidates are staged
@@ -431,20 +377,31 @@ __global__ void __launch_bounds__(LC_THREADS) k_list_cells(
     }
 }
 
-// All pairs of different molecules (small boxes), warp per atom, identity order.
+// Small boxes (no cell grid), warp per atom, identity order: every atom of another
+// molecule whose minimum-image anchor distance is below r_list, by brute force with the
+// same FP64 operation order as the cell path.  The pair kernel then applies a per-bead
+// minimum image, which r_list >= L/2 makes necessary.
 template <bool FILL>
-__global__ void k_list_all(const int* flag, int N, double L, const int* mol_s, const int* type_s, const double* anchor,
-                           int* count, const int* start, int4* nbr, int row_cap, unsigned* status) {
+__global__ void k_list_all(const int* flag, int N, double L, double r2max, const int* mol_s, const int* type_s,
+                           const double* anchor, int* count, const int* start, int4* nbr, int row_cap,
+                           unsigned* status) {
     if (!*flag) return;
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= N) return;
     const int mi = mol_s[i];
+    const double Ax = anchor[i * 3], Ay = anchor[i * 3 + 1], Az = anchor[i * 3 + 2];
     int cnt = 0;
     const int base = FILL ? start[i] : 0;
     for (int jb = 0; jb < N; jb += 32) {
         const int j = jb + lane;
-        const bool acc = j < N && mol_s[j] != mi;
+        bool acc = j < N && mol_s[j] != mi;
+        if (acc) {
+            const double ex = min_image_rn(__dsub_rn(anchor[j * 3], Ax), L);
+            const double ey = min_image_rn(__dsub_rn(anchor[j * 3 + 1], Ay), L);
+            const double ez = min_image_rn(__dsub_rn(anchor[j * 3 + 2], Az), L);
+            acc = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) < r2max;
+        }
         const unsigned bal = __ballot_sync(0xffffffffu, acc);
         if (FILL && acc) {
             const int pos = base + cnt + __popc(bal & ((1u << lane) - 1u));
@@ -472,6 +429,11 @@ cudaError_t launch_list_check(qhp_system_s* s, bool force) {
     s->launches++;
     k_check<<<1, 1, 0, s->stream>>>(s->dev_max, half * half, s->rebuild_flag, force ? 1 : 0, s->rebuild_count,
                                     s->cond_handle, s->cond_active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_batch(const CheckArgs* args, int n, cudaStream_t stream) {
+    k_check_batch<<<(n + 127) / 128, 128, 0, stream>>>(args, n);
     return cudaGetLastError();
 }
 
@@ -514,7 +476,7 @@ cudaError_t launch_rebuild(qhp_system_s* s) {
                                                          s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor,
                                                          s->nbr_count, s->nbr_start, s->nbr, s->row_cap, s->status);
     } else {
-        k_list_all<true><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, s->nbr_start,
+        k_list_all<true><<<gW, wb, 0, st>>>(flag, N, s->L, r2max, s->mol_s, s->type_s, s->anchor, s->nbr_count, s->nbr_start,
                                             s->nbr, s->row_cap, s->status);
     }
     s->launches += 2;
@@ -553,7 +515,7 @@ int host_list_size(qhp_system_s* s, int64_t* max_row) {
                                                           s->cell_start, s->cw, s->cwl, s->mol_s, s->type_s, s->anchor,
                                                           s->nbr_count, nullptr, nullptr, 0, s->status);
     else
-        k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr,
+        k_list_all<false><<<gW, wb, 0, st>>>(flag, N, s->L, r2max, s->mol_s, s->type_s, s->anchor, s->nbr_count, nullptr,
                                              nullptr, 0, s->status);
     s->launches += 9;
     QHP_CUDA(cudaGetLastError());

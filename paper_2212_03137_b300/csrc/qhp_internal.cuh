@@ -189,6 +189,7 @@ struct qhp_system_s {
     unsigned long long* step_ctr = nullptr;                  // device copy of the step counter
     int64_t rebuilds_host = 0;
     int keep_anchor = 0;           // 1 while a checkpoint restore rebuilds from stored anchors
+    int pair_w = 0;                // warps per atom of the mixed pair kernel (0: default for P)
     int prof_on = 0;               // per-stage events recorded inside each step
     int use_graphs = 1;            // 0: launch each step's kernels directly
     cudaGraphConditionalHandle cond_handle = 0;   // IF node around the rebuild chain of the step graph
@@ -303,6 +304,42 @@ cudaError_t launch_gather_centroids(qhp_system_s* s, double* out);
 cudaError_t launch_step_counter(qhp_system_s* s);
 int host_list_size(qhp_system_s* s, int64_t* max_row);
 int rebuild_list_now(qhp_system_s* s);   // synchronous; checks the beads are covered
+void graph_invalidate(qhp_system_s* s);  // drop the captured step graph (its parameters changed)
+int system_sync(qhp_system_s* s);        // synchronise the system's stream, report its status
+
+// One stage of a batched step over many systems: the stage's per-system argument
+// records, its (system, block) work items in system order, and the contiguous item
+// range of every block of a persistent grid (ranges[g] .. ranges[g + 1]).
+struct BatchStage {
+    void* args = nullptr;
+    int2* items = nullptr;
+    int* ranges = nullptr;
+    int grid = 0, n_items = 0;
+    size_t smem = 0;
+    double cost = 0.0;   // estimated work of the whole stage (arbitrary units)
+};
+// Upload a stage: split the items into `grid` contiguous ranges of about equal cost.
+int stage_upload(BatchStage& st, const void* args, size_t args_bytes, const std::vector<int2>& items,
+                 const std::vector<double>& cost, int grid);
+void stage_free(BatchStage& st);
+int sm_count();
+int batch_stage_integrate(const std::vector<qhp_system_s*>& v, BatchStage& st);
+int batch_stage_project(const std::vector<qhp_system_s*>& v, BatchStage& st);
+int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[7], by log2 P*/);
+int batch_stage_bonded(const std::vector<qhp_system_s*>& v, BatchStage& st);
+cudaError_t launch_batch_integrate(const BatchStage& st, cudaStream_t stream);
+cudaError_t launch_batch_project(const BatchStage& st, cudaStream_t stream);
+cudaError_t launch_batch_pair(const BatchStage* st /*[7]*/, cudaStream_t stream);   // one launch per P
+cudaError_t launch_batch_bonded(const BatchStage& st, cudaStream_t stream);
+// Per-system record of the batched list check (the single-system k_check, one thread each).
+struct CheckArgs {
+    unsigned* dev_max;
+    int* flag;
+    unsigned* rebuild_count;
+    cudaGraphConditionalHandle cond;
+    float thr2;
+};
+cudaError_t launch_check_batch(const CheckArgs* args, int n, cudaStream_t stream);
 int compute_energy(qhp_system_s* s, qhp_energy* out);
 int beads_fp64(qhp_system_s* s, double* dev_out);
 cudaError_t launch_estimators(qhp_system_s* s, double* partial, int* nblocks);

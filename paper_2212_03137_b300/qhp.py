@@ -91,6 +91,16 @@ _SIGS = {
     "qhp_count_pairs": [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "qhp_estimators_noalloc": [C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP],
     "qhp_get_list_row": [_VP, C.c_int, _IP, C.c_int, _IP],
+    "qhp_create_batch": [C.POINTER(_VP), C.c_int, C.POINTER(_VP)],
+    "qhp_destroy_batch": [_VP],
+    "qhp_batch_step": [_VP, C.c_int],
+    "qhp_batch_sync": [_VP],
+    "qhp_batch_set_stream": [_VP, _VP],
+    "qhp_batch_autotune": [_VP, C.c_int, _IP],
+    "qhp_batch_get_info": [_VP, _VP],
+    "qhp_batch_get_profile": [_VP, _VP],
+    "qhp_autotune": [_VP, C.c_int, _IP],
+    "qhp_set_pair_warps": [_VP, C.c_int],
     "qhp_energy_grad": [_VP, _DP, _DP, _DP],
     "qhp_energy_grad_device": [_VP, _VP, _DP, _VP, _DP],
     "qhp_segment_grad": [_VP, C.c_int, C.c_int, C.c_int, _DP, _DP],
@@ -347,6 +357,96 @@ def qhp_count_pairs(h) -> tuple[int, int]:
 
 
 # ------------------------------------------------------------------ convenience
+
+class qhp_batch_info(C.Structure):
+    _fields_ = [("n_sys", C.c_int), ("kernels_per_step", C.c_int), ("atom_beads", C.c_int64), ("steps", C.c_int64),
+                ("rebuilds", C.c_int64), ("kernel_launches", C.c_int64), ("grid_integrate", C.c_int),
+                ("grid_pair", C.c_int), ("grid_bonded", C.c_int), ("grid_project", C.c_int), ("items_pair", C.c_int),
+                ("reserved", C.c_int)]
+
+
+def qhp_create_batch(handles) -> int:
+    arr = (_VP * len(handles))(*handles)
+    b = _VP()
+    _check(lib().qhp_create_batch(C.byref(b), len(handles), arr))
+    return b
+
+
+def qhp_destroy_batch(b) -> None:
+    _check(lib().qhp_destroy_batch(b))
+
+
+def qhp_batch_step(b, n: int) -> None:
+    _check(lib().qhp_batch_step(b, int(n)))
+
+
+def qhp_batch_sync(b) -> None:
+    _check(lib().qhp_batch_sync(b))
+
+
+def qhp_batch_set_stream(b, stream_ptr: int | None) -> None:
+    _check(lib().qhp_batch_set_stream(b, C.c_void_p(stream_ptr or 0)))
+
+
+def qhp_batch_autotune(b, reps: int = 5) -> dict:
+    """Tuned warps per atom by bead count, {P: W}."""
+    out = (C.c_int * 7)()
+    _check(lib().qhp_batch_autotune(b, int(reps), out))
+    return {1 << k: out[k] for k in range(7) if out[k]}
+
+
+def qhp_batch_get_info(b) -> qhp_batch_info:
+    info = qhp_batch_info()
+    _check(lib().qhp_batch_get_info(b, C.cast(C.byref(info), C.c_void_p)))
+    return info
+
+
+def qhp_batch_get_profile(b):
+    p = qhp_profile()
+    _check(lib().qhp_batch_get_profile(b, C.cast(C.byref(p), C.c_void_p)))
+    return p
+
+
+def qhp_autotune(h, reps: int = 5) -> int:
+    w = C.c_int(0)
+    _check(lib().qhp_autotune(h, int(reps), C.byref(w)))
+    return w.value
+
+
+def qhp_set_pair_warps(h, w: int) -> None:
+    _check(lib().qhp_set_pair_warps(h, int(w)))
+
+
+class Batch:
+    """Owns one qhp_batch over caller-owned System objects (kept alive here)."""
+
+    def __init__(self, systems):
+        self.systems = list(systems)
+        self.h = qhp_create_batch([s.h for s in self.systems])
+
+    def step(self, n: int) -> None:
+        qhp_batch_step(self.h, n)
+
+    def sync(self) -> None:
+        qhp_batch_sync(self.h)
+
+    def close(self):
+        if self.h is not None:
+            qhp_destroy_batch(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 PARAM_NAMES = ("eps", "sigma", "q_O", "k_b", "k_theta")
 

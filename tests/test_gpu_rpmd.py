@@ -70,6 +70,24 @@ def test_cells_and_centroid_list_bit_exact(cfg):
         assert set(map(tuple, got.tolist())) == list_pairs_oracle(C, box.molecule, box.box, r_list)
 
 
+@pytest.mark.parametrize("cfg", [C1, CONFIGS["grad_216w"]], ids=["64w_L12.42", "216w_L18.6"])
+def test_small_box_list_bit_exact(cfg):
+    """Boxes with r_list >= L/2 have no cell grid: the rows still hold exactly the pairs of
+    different molecules whose minimum-image centroid distance is below r_list."""
+    with _sys(cfg) as s:
+        for n in (0, 15):
+            qhp.qhp_step_rpmd(s.h, n)
+            qhp.qhp_build_list(s.h)
+            assert qhp.qhp_get_info(s.h).list_mode == 0
+            Q, _ = qhp.qhp_get_modes(s.h)
+            box = cfg.system()
+            got = set(map(tuple, qhp.qhp_get_list_pairs(s.h).tolist()))
+            ref = list_pairs_oracle(Q[:, :, 0], box.molecule, box.box, cfg.rc + cfg.skin)
+            assert got == ref
+            n_mol_pairs = cfg.n_mol * (cfg.n_mol - 1) // 2 * 9
+            assert len(ref) < n_mol_pairs   # the distance filter removes pairs
+
+
 def test_list_after_dynamics_and_edge_positions():
     """Centroids moved by dynamics and pushed onto cell/box boundaries: still bit-exact."""
     cfg = SMALL
