@@ -15,8 +15,14 @@
 // The convolution is a 4N-point circular FFT convolution that equals the linear one
 // on the N outputs kept.  Two real dofs ride in one complex FFT (a + i b): with X the
 // transform, A_k = (X_k + X*_{-k})/2 and B_k = (X_k - X*_{-k})/(2i).
+//
+// FFTs are in place in shared memory, radix 2^2 (two radix-2 stages per pass, so half
+// the passes and barriers of radix 2): the forward transform is decimation in frequency
+// (natural order in, bit-reversed out) and the inverse decimation in time (bit-reversed
+// in, natural out), so the pointwise product in between needs no permutation pass.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "qhp_internal.cuh"
@@ -34,33 +40,96 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 
 __device__ __forceinline__ int brev(int j, int logn) { return (int)(__brev((unsigned)j) >> (32 - logn)); }
 
-// In-place radix-2 decimation-in-time FFT of n points already in bit-reversed order.
-// tw[k] = exp(-2 pi i k / n), k < n/2.  sign = -1 forward, +1 inverse (unscaled).
-__device__ void fft_dit(float2* buf, int n, const float2* __restrict__ tw, int sign) {
-    for (int h = 1; h < n; h <<= 1) {
+// The spectrum of a real signal pairs bin k with bin -k.  In bit-reversed storage (the
+// forward FFT's output) position p = brev(k) has its partner -k at the mirror of p
+// within p's power-of-two block [b, 2b): pm = 3b - 1 - p.  Item q in [0, n/2] visits each
+// pair once with p in the lower half of its block, so consecutive q read consecutive p
+// and consecutive (descending) pm: no shared-memory bank conflicts.
+__device__ __forceinline__ void pair_positions(int q, int& p, int& pm) {
+    if (q < 2) {
+        p = pm = q;   // k = 0 and k = n/2 are their own partners
+        return;
+    }
+    const int qq = q - 1;
+    const int b = 2 << (31 - __clz(qq));
+    p = qq + (b >> 1);
+    pm = 3 * b - 1 - p;
+}
+
+// Forward FFT in place, natural order in, bit-reversed order out (radix-2 decimation in
+// frequency, stages fused in pairs).  tw[k] = exp(-2 pi i k / n), k < n/2.  NB buffers
+// of n points are transformed together (more independent work per barrier).
+template <int NB>
+__device__ void fft_dif_fwd(float2* const (&x)[NB], int n, int logn, const float2* __restrict__ tw) {
+    int h = n >> 1, lh = logn - 1, s = 1;   // stage half-size h = 2^lh, twiddle stride n/(2h)
+    for (; h >= 2; h >>= 2, lh -= 2, s <<= 2) {
         __syncthreads();
-        const int stride = n / (2 * h);
-        for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
-            const int pos = t & (h - 1);
-            const int i0 = ((t - pos) << 1) + pos, i1 = i0 + h;
-            float2 w = __ldg(&tw[pos * stride]);
-            if (sign > 0) w.y = -w.y;
-            const float2 a = buf[i0], b = cmul(buf[i1], w);
-            buf[i0] = cadd(a, b);
-            buf[i1] = csub(a, b);
+        const int lq = lh - 1;              // q < h/2 = 2^lq
+        for (int g = threadIdx.x; g < (n >> 2); g += blockDim.x) {
+            const int q = g & ((1 << lq) - 1);
+            const int i0 = ((g >> lq) << (lh + 1)) + q, i1 = i0 + (h >> 1), i2 = i0 + h, i3 = i2 + (h >> 1);
+            const float2 wA = __ldg(&tw[q * s]), wB = __ldg(&tw[2 * q * s]);
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                float2* X = x[u];
+                const float2 a0 = X[i0], a1 = X[i1], a2 = X[i2], a3 = X[i3];
+                const float2 t0 = cadd(a0, a2), t2 = cmul(csub(a0, a2), wA);
+                const float2 t1 = cadd(a1, a3);
+                float2 t3 = cmul(csub(a1, a3), wA);
+                t3 = make_float2(t3.y, -t3.x);   // times W^{n/4} = -i
+                X[i0] = cadd(t0, t1);
+                X[i1] = cmul(csub(t0, t1), wB);
+                X[i2] = cadd(t2, t3);
+                X[i3] = cmul(csub(t2, t3), wB);
+            }
+        }
+    }
+    if (h == 1) {   // odd number of stages: the last one alone (unit twiddles)
+        __syncthreads();
+        for (int g = threadIdx.x; g < (n >> 1); g += blockDim.x) {
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                float2* X = x[u];
+                const float2 a = X[2 * g], b = X[2 * g + 1];
+                X[2 * g] = cadd(a, b);
+                X[2 * g + 1] = csub(a, b);
+            }
         }
     }
     __syncthreads();
 }
 
-__device__ void bitrev_permute(float2* buf, int n, int logn) {
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int r = brev(j, logn);
-        if (j < r) {
-            const float2 t = buf[j];
-            buf[j] = buf[r];
-            buf[r] = t;
+// Inverse FFT in place (unscaled), bit-reversed order in, natural order out (radix-2
+// decimation in time with conjugate twiddles, stages fused in pairs).
+__device__ void fft_dit_inv(float2* x, int n, int logn, const float2* __restrict__ tw) {
+    int h = 1, lh = 0, s = n >> 1;          // stage half-size h = 2^lh, twiddle stride n/(2h)
+    if (logn & 1) {                         // odd number of stages: the first one alone
+        __syncthreads();
+        for (int g = threadIdx.x; g < (n >> 1); g += blockDim.x) {
+            const float2 a = x[2 * g], b = x[2 * g + 1];
+            x[2 * g] = cadd(a, b);
+            x[2 * g + 1] = csub(a, b);
+        }
+        h = 2;
+        lh = 1;
+        s = n >> 2;
+    }
+    for (; h < n; h <<= 2, lh += 2, s >>= 2) {   // stages h and 2h
+        __syncthreads();
+        for (int g = threadIdx.x; g < (n >> 2); g += blockDim.x) {
+            const int q = g & (h - 1);
+            const int i0 = ((g >> lh) << (lh + 2)) + q, i1 = i0 + h, i2 = i0 + 2 * h, i3 = i0 + 3 * h;
+            const float2 w1 = cconj(__ldg(&tw[q * s])), w2 = cconj(__ldg(&tw[q * (s >> 1)]));
+            const float2 a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
+            const float2 b1 = cmul(a1, w1), b3 = cmul(a3, w1);
+            const float2 u0 = cadd(a0, b1), u1 = csub(a0, b1), u2 = cadd(a2, b3), u3 = csub(a2, b3);
+            const float2 c2 = cmul(u2, w2);
+            float2 c3 = cmul(u3, w2);
+            c3 = make_float2(-c3.y, c3.x);       // times W^{-n/4} = +i
+            x[i0] = cadd(u0, c2);
+            x[i2] = csub(u0, c2);
+            x[i1] = cadd(u1, c3);
+            x[i3] = csub(u1, c3);
         }
     }
     __syncthreads();
@@ -72,17 +141,19 @@ __device__ __forceinline__ float2 white_pair(uint64_t seed, uint32_t dof, uint64
     return make_float2(normal_f32(x, 0), normal_f32(x, 1));
 }
 
-constexpr int GEN_PAIRS = 4;   // dof pairs per block -> 8 dofs = 32-byte output rows
+constexpr int GEN_PAIRS = 4;     // dof pairs per block -> 8 dofs = 32-byte output rows
+constexpr int GEN_THREADS = 512;
 
 // One colored-noise segment k for all dofs.
-__global__ void __launch_bounds__(256) k_qtb_generate(int n_dof, int N, int log4n, int64_t seg, uint64_t seed,
-                                                      const int* __restrict__ dof_type,
-                                                      const float2* __restrict__ H /*[2][4N]*/,
-                                                      const float2* __restrict__ tw4, float* __restrict__ u) {
+__global__ void __launch_bounds__(GEN_THREADS) k_qtb_generate(int n_dof, int N, int log4n, int64_t seg,
+                                                              uint64_t seed, const int* __restrict__ dof_type,
+                                                              const float2* __restrict__ H /*[2][4N]*/,
+                                                              const float2* __restrict__ tw4, float* __restrict__ u) {
     extern __shared__ float2 sm[];
     const int n = 4 * N;
     float2* buf = sm;                                  // [4N]
     float* stage = reinterpret_cast<float*>(sm + n);   // [N][8]
+    float2* const bufs[1] = {buf};
     const int pair0 = blockIdx.x * GEN_PAIRS;
     for (int pp = 0; pp < GEN_PAIRS; ++pp) {
         const int da = 2 * (pair0 + pp), db = da + 1;
@@ -96,26 +167,28 @@ __global__ void __launch_bounds__(256) k_qtb_generate(int n_dof, int N, int log4
                 if (va) xa = white_pair(seed, (uint32_t)da, gs);
                 if (vb) xb = white_pair(seed, (uint32_t)db, gs);
             }
-            buf[brev(t, log4n)] = make_float2(xa.x, xb.x);
-            buf[brev(t + 1, log4n)] = make_float2(xa.y, xb.y);
+            buf[t] = make_float2(xa.x, xb.x);
+            buf[t + 1] = make_float2(xa.y, xb.y);
         }
-        fft_dit(buf, n, tw4, -1);
+        fft_dif_fwd<1>(bufs, n, log4n, tw4);   // bin k now sits at position brev(k)
         const int za = va ? dof_type[da] : 0, zb = vb ? dof_type[db] : 0;
-        for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
-            const int km = (n - k) & (n - 1);
-            const float2 Xk = buf[k], Xm = buf[km];
+        const float2* Ha = H + za * n;           // H is stored in the same bit-reversed order
+        const float2* Hb = H + zb * n;
+        for (int q = threadIdx.x; q <= n / 2; q += blockDim.x) {
+            int pk, pm;
+            pair_positions(q, pk, pm);
+            const float2 Xk = buf[pk], Xm = buf[pm];
             const float2 Ak = make_float2(0.5f * (Xk.x + Xm.x), 0.5f * (Xk.y - Xm.y));   // (X_k + X*_-k)/2
             const float2 Bk = make_float2(0.5f * (Xk.y + Xm.y), -0.5f * (Xk.x - Xm.x));  // (X_k - X*_-k)/(2i)
-            const float2 Yk = cadd(cmul(H[za * n + k], Ak), cmul(make_float2(0.f, 1.f), cmul(H[zb * n + k], Bk)));
-            if (km != k) {
+            const float2 Yk = cadd(cmul(Ha[pk], Ak), cmul(make_float2(0.f, 1.f), cmul(Hb[pk], Bk)));
+            if (pm != pk) {
                 const float2 Am = cconj(Ak), Bm = cconj(Bk);                                 // spectra of real signals
-                const float2 Ym = cadd(cmul(H[za * n + km], Am), cmul(make_float2(0.f, 1.f), cmul(H[zb * n + km], Bm)));
-                buf[km] = Ym;
+                const float2 Ym = cadd(cmul(Ha[pm], Am), cmul(make_float2(0.f, 1.f), cmul(Hb[pm], Bm)));
+                buf[pm] = Ym;
             }
-            buf[k] = Yk;
+            buf[pk] = Yk;
         }
-        bitrev_permute(buf, n, log4n);
-        fft_dit(buf, n, tw4, +1);
+        fft_dit_inv(buf, n, log4n, tw4);
         const float inv = 1.0f / (float)n;
         for (int m = threadIdx.x; m < N; m += blockDim.x) {
             const float2 y = buf[N + m];
@@ -132,87 +205,129 @@ __global__ void __launch_bounds__(256) k_qtb_generate(int n_dof, int N, int log4
     }
 }
 
-// Per-block sums over dof pairs of: Delta (needs gamma), C_vv, Re C_vF, per type and bin.
-__global__ void __launch_bounds__(256) k_qtb_spectra(int n_dof, int N, int log2n, double dt, const int* __restrict__ dof_type,
-                                                     const double* __restrict__ m_dof, const double* __restrict__ gamma,
-                                                     const float* __restrict__ v, const float* __restrict__ F,
-                                                     const float2* __restrict__ tw2, double* __restrict__ part) {
-    extern __shared__ float2 sm[];
-    const int n = 2 * N, nb = N + 1;
-    float2* bv = sm;
-    float2* bf = sm + n;
-    double* acc = reinterpret_cast<double*>(sm + 2 * n);   // [3][2][nb]
-    for (int e = threadIdx.x; e < 6 * nb; e += blockDim.x) acc[e] = 0.0;
-    const int n_pairs = (n_dof + 1) / 2;
-    const double norm = dt / (double)N;
-    for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
-        const int da = 2 * p, db = da + 1;
-        const bool vb = db < n_dof;
-        __syncthreads();
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            float2 xv = make_float2(0.f, 0.f), xf = make_float2(0.f, 0.f);
-            if (t < N) {
-                xv.x = v[(size_t)t * n_dof + da];
-                xf.x = F[(size_t)t * n_dof + da];
-                if (vb) {
-                    xv.y = v[(size_t)t * n_dof + db];
-                    xf.y = F[(size_t)t * n_dof + db];
-                }
-            }
-            const int r = brev(t, log2n);
-            bv[r] = xv;
-            bf[r] = xf;
-        }
-        fft_dit(bv, n, tw2, -1);
-        fft_dit(bf, n, tw2, -1);
-        const int za = dof_type[da], zb = vb ? dof_type[db] : 0;
-        const double ma = m_dof[da], mb = vb ? m_dof[db] : 0.0;
-        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-            const int km = (n - k) & (n - 1);
-            const float2 Xk = bv[k], Xm = bv[km], Yk = bf[k], Ym = bf[km];
-            // a-signal and b-signal spectra at bin k
-            const double var = 0.5 * ((double)Xk.x + Xm.x), vai = 0.5 * ((double)Xk.y - Xm.y);
-            const double vbr = 0.5 * ((double)Xk.y + Xm.y), vbi = -0.5 * ((double)Xk.x - Xm.x);
-            const double far_ = 0.5 * ((double)Yk.x + Ym.x), fai = 0.5 * ((double)Yk.y - Ym.y);
-            const double fbr = 0.5 * ((double)Yk.y + Ym.y), fbi = -0.5 * ((double)Yk.x - Ym.x);
-            {
-                const double cvv = norm * (var * var + vai * vai);
-                const double cvf = norm * (var * far_ + vai * fai);    // Re(v F*)
-                const double dl = (ma * gamma[za * nb + k] * cvv - cvf) / ACC;
-                acc[(0 * 2 + za) * nb + k] += dl;
-                acc[(1 * 2 + za) * nb + k] += cvv;
-                acc[(2 * 2 + za) * nb + k] += cvf;
-            }
-            if (vb) {
-                const double cvv = norm * (vbr * vbr + vbi * vbi);
-                const double cvf = norm * (vbr * fbr + vbi * fbi);
-                const double dl = (mb * gamma[zb * nb + k] * cvv - cvf) / ACC;
-                acc[(0 * 2 + zb) * nb + k] += dl;
-                acc[(1 * 2 + zb) * nb + k] += cvv;
-                acc[(2 * 2 + zb) * nb + k] += cvf;
-            }
-        }
+constexpr int SPEC_THREADS = 256;
+constexpr int SPEC_DOFS = 4;   // dofs per tile: 16-byte row segments of v and F
+
+// acc[z] += a, acc[2 + z] += b with constant indices (registers, not memory)
+__device__ __forceinline__ void add_typed(float* acc, int z, float a, float b) {
+    if (z == 0) {
+        acc[0] += a;
+        acc[2] += b;
+    } else {
+        acc[1] += a;
+        acc[3] += b;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < 6 * nb; e += blockDim.x) part[(size_t)blockIdx.x * 6 * nb + e] = acc[e];
 }
 
-// Sum the block partials in fixed order, then adapt gamma per type and bin.
-__global__ void k_qtb_adapt(int nblocks, int N, const double* __restrict__ part, double n_O, double n_H,
+// Per-block sums over dofs of |v~_k|^2 and Re(v~_k F~_k*) per type and bin (Eq. (22) without
+// its dt/N factor; the per-type FDT deviation is linear in them and is formed from the
+// sums in k_qtb_adapt).  Each thread owns the bins k = t, t + 256, ... (at most BPT): a
+// tile of 4 dofs is summed in FP32, then added to FP64 running sums.  The block walks
+// tiles of 4 dofs, read as [step][4] rows.
+template <int BPT>
+__global__ void __launch_bounds__(SPEC_THREADS) k_qtb_spectra(int n_dof, int N, int log2n,
+                                                              const int* __restrict__ dof_type,
+                                                              const float* __restrict__ v, const float* __restrict__ F,
+                                                              const float2* __restrict__ tw2,
+                                                              double* __restrict__ part) {
+    extern __shared__ float2 sm[];
+    const int n = 2 * N, nb = N + 1;
+    float2* bv = sm;                                         // [2N]
+    float2* bf = sm + n;                                     // [2N]
+    float* tv = reinterpret_cast<float*>(sm + 2 * n);        // [N][4]
+    float* tf = tv + N * SPEC_DOFS;                          // [N][4]
+    float2* const bufs[2] = {bv, bf};
+    double acc[BPT][4];
+#pragma unroll
+    for (int j = 0; j < BPT; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = 0.0;
+    const int n_tiles = (n_dof + SPEC_DOFS - 1) / SPEC_DOFS;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int d0 = tile * SPEC_DOFS;
+        __syncthreads();
+        for (int e = threadIdx.x; e < N * SPEC_DOFS; e += blockDim.x) {
+            const int m = e / SPEC_DOFS, c = e % SPEC_DOFS;
+            const bool ok = d0 + c < n_dof;
+            tv[e] = ok ? v[(size_t)m * n_dof + d0 + c] : 0.0f;
+            tf[e] = ok ? F[(size_t)m * n_dof + d0 + c] : 0.0f;
+        }
+        float ts[BPT][4];
+#pragma unroll
+        for (int j = 0; j < BPT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ts[j][q] = 0.0f;
+        for (int pp = 0; pp < SPEC_DOFS / 2; ++pp) {
+            const int da = d0 + 2 * pp, db = da + 1;
+            if (da >= n_dof) break;
+            const bool vb = db < n_dof;
+            __syncthreads();
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                float2 xv = make_float2(0.f, 0.f), xf = make_float2(0.f, 0.f);
+                if (t < N) {
+                    xv = make_float2(tv[t * SPEC_DOFS + 2 * pp], tv[t * SPEC_DOFS + 2 * pp + 1]);
+                    xf = make_float2(tf[t * SPEC_DOFS + 2 * pp], tf[t * SPEC_DOFS + 2 * pp + 1]);
+                }
+                bv[t] = xv;
+                bf[t] = xf;
+            }
+            fft_dif_fwd<2>(bufs, n, log2n, tw2);   // bin k at position brev(k)
+            const int za = dof_type[da], zb = vb ? dof_type[db] : 0;
+#pragma unroll
+            for (int j = 0; j < BPT; ++j) {
+                const int q = threadIdx.x + j * SPEC_THREADS;
+                if (q >= nb) break;
+                int pk, pm;
+                pair_positions(q, pk, pm);
+                const float2 Xk = bv[pk], Xm = bv[pm], Yk = bf[pk], Ym = bf[pm];
+                // spectra of the a and b signals at bin k (twice their values: the 1/2 of
+                // the real-pair split is applied squared, as 1/4, below)
+                const float var = Xk.x + Xm.x, vai = Xk.y - Xm.y, vbr = Xk.y + Xm.y, vbi = Xm.x - Xk.x;
+                const float far_ = Yk.x + Ym.x, fai = Yk.y - Ym.y, fbr = Yk.y + Ym.y, fbi = Ym.x - Yk.x;
+                add_typed(ts[j], za, 0.25f * (var * var + vai * vai), 0.25f * (var * far_ + vai * fai));
+                if (vb) add_typed(ts[j], zb, 0.25f * (vbr * vbr + vbi * vbi), 0.25f * (vbr * fbr + vbi * fbi));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < BPT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[j][q] += (double)ts[j][q];
+    }
+    // part[block][c][bin], c = (vv O, vv H, vF O, vF H); slot j holds bin min(k, n - k) of
+    // the pair visited by item q
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) {
+        const int q = threadIdx.x + j * SPEC_THREADS;
+        if (q >= nb) break;
+        int pk, pm;
+        pair_positions(q, pk, pm);
+        const int k = brev(pk, log2n), bin = min(k, n - k);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[((size_t)blockIdx.x * 4 + c) * nb + bin] = acc[j][c];
+    }
+}
+
+// Sum the block partials in fixed order, form the type means C_vv, C_vF (with the dt/N
+// factor) and the FDT deviation Delta = (m gamma C_vv - Re C_vF) / 418.4 (Eq. (21); linear
+// in the spectra, so the mean of the per-dof deviations), then adapt gamma.
+__global__ void k_qtb_adapt(int nblocks, int N, double norm, const double* __restrict__ part, double n_O, double n_H,
                             double m_O, double m_H, int adapt, double a_gamma, double gmin, double wavg, int first,
                             double* gamma, double* avg, double* delta_out) {
     const int nb = N + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;   // (type, bin)
     if (e >= 2 * nb) return;
     const int z = e / nb, k = e % nb;
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < nblocks; ++b)
-        for (int q = 0; q < 3; ++q) s[q] += part[(size_t)b * 6 * nb + (q * 2 + z) * nb + k];
+    double svv = 0.0, svf = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        svv += part[((size_t)b * 4 + z) * nb + k];
+        svf += part[((size_t)b * 4 + 2 + z) * nb + k];
+    }
     const double cnt = z == 0 ? n_O : n_H;
     if (cnt <= 0.0) return;
-    const double dbar = s[0] / cnt, cvv = s[1] / cnt, cvf = s[2] / cnt;
-    delta_out[z * nb + k] = dbar;
+    const double cvv = norm * svv / cnt, cvf = norm * svf / cnt;
     double g = gamma[z * nb + k];
+    const double dbar = ((z == 0 ? m_O : m_H) * g * cvv - cvf) / ACC;
+    delta_out[z * nb + k] = dbar;
     if (adapt == QHP_ADAPT_SIMPLE) {
         g = g - a_gamma * dbar;
     } else if (adapt == QHP_ADAPT_RATIO) {
@@ -246,31 +361,49 @@ __global__ void k_qtb_sqrtS(int N, double dt, double kT, double hbar, double gam
     sqrtS[e] = sqrt(S);
 }
 
-// Filter taps of each type for the next segment: h_l, l in [-N, N).
-__global__ void k_qtb_taps(int N, const double* __restrict__ sqrtS, double* __restrict__ h /*[2][2N]*/) {
+constexpr int TAP_THREADS = 128;
+
+// Fixed-order block sum of one double per thread (TAP_THREADS threads).
+__device__ __forceinline__ double block_sum(double x, double* sh) {
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = TAP_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+// Filter taps of each type for the next segment: h_l, l in [-N, N); one block per tap.
+__global__ void __launch_bounds__(TAP_THREADS) k_qtb_taps(int N, const double* __restrict__ sqrtS,
+                                                          double* __restrict__ h /*[2][2N]*/) {
+    __shared__ double sh[TAP_THREADS];
     const int nf = 2 * N, nb = N + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * nf) return;
+    const int e = blockIdx.x;
     const int z = e / nf, li = e % nf;       // l = li - N
     const long long l = li - N;
     double acc = 0.0;
-    for (int j = 0; j < nf; ++j) {
+    for (int j = threadIdx.x; j < nf; j += TAP_THREADS) {
         const int bin = j < nf - j ? j : nf - j;
         long long jl = ((long long)j * l) % nf;
         if (jl < 0) jl += nf;
         acc += sqrtS[z * nb + bin] * cospi(2.0 * (double)jl / (double)nf);
     }
-    h[e] = acc / nf;
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) h[e] = acc / nf;
 }
 
-__global__ void k_qtb_filter(int N, const double* __restrict__ h, float2* __restrict__ H /*[2][4N]*/) {
+// Transfer function of the taps on the 4N-point grid (taps at circular index l mod 4N);
+// one block per (type, bin).
+__global__ void __launch_bounds__(TAP_THREADS) k_qtb_filter(int N, int log4n, const double* __restrict__ h,
+                                                            float2* __restrict__ H /*[2][4N], bit-reversed bins*/) {
+    __shared__ double sh[TAP_THREADS];
     const int n = 4 * N, nf = 2 * N;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * n) return;
+    const int e = blockIdx.x;
     const int z = e / n, k = e % n;
     double re = 0.0, im = 0.0;
-    for (int li = 0; li < nf; ++li) {
-        const long long l = li - N;                       // tap at circular index l mod 4N
+    for (int li = threadIdx.x; li < nf; li += TAP_THREADS) {
+        const long long l = li - N;
         long long kl = ((long long)k * l) % n;
         if (kl < 0) kl += n;
         double sn, cs;
@@ -278,7 +411,10 @@ __global__ void k_qtb_filter(int N, const double* __restrict__ h, float2* __rest
         re += h[z * nf + li] * cs;
         im -= h[z * nf + li] * sn;
     }
-    H[e] = make_float2((float)re, (float)im);
+    re = block_sum(re, sh);
+    __syncthreads();
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) H[z * n + brev(k, log4n)] = make_float2((float)re, (float)im);
 }
 
 int ilog2(int n) {
@@ -301,8 +437,56 @@ int qalloc(qhp_system_s* s, T** p, size_t count) {
 }
 
 size_t gen_smem(int N) { return sizeof(float2) * 4 * N + sizeof(float) * 8 * N; }
-size_t spec_smem(int N) { return sizeof(float2) * 4 * N + sizeof(double) * 6 * (N + 1); }
+size_t spec_smem(int N) { return sizeof(float2) * 4 * N + sizeof(float) * 2 * SPEC_DOFS * N; }
 constexpr int SPEC_BLOCKS = 592;
+
+// bins per thread of the spectra kernel for N (n_seg <= 2048): ceil((N + 1) / 256)
+int spec_bpt(int N) {
+    const int b = (N + 1 + SPEC_THREADS - 1) / SPEC_THREADS;
+    return b <= 1 ? 1 : b <= 2 ? 2 : b <= 3 ? 3 : b <= 5 ? 5 : 9;
+}
+
+template <int B>
+const void* spectra_kernel() { return (const void*)k_qtb_spectra<B>; }
+
+const void* spectra_kernel_for(int N) {
+    switch (spec_bpt(N)) {
+        case 1: return spectra_kernel<1>();
+        case 2: return spectra_kernel<2>();
+        case 3: return spectra_kernel<3>();
+        case 5: return spectra_kernel<5>();
+        default: return spectra_kernel<9>();
+    }
+}
+
+// Resident blocks of the spectra kernel (one wave; every block walks many tiles).
+int spectra_blocks(qhp_system_s* s) {
+    const int N = s->n_seg, n_dof = 3 * s->N;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spectra_kernel_for(N), SPEC_THREADS, spec_smem(N)) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int n_tiles = (n_dof + SPEC_DOFS - 1) / SPEC_DOFS;
+    return std::max(1, std::min(std::min(SPEC_BLOCKS, n_tiles), per_sm * sm_count()));
+}
+
+cudaError_t launch_spectra(qhp_system_s* s, int blocks) {
+    const int N = s->n_seg, n_dof = 3 * s->N;
+    const size_t sm = spec_smem(N);
+#define QHP_SPEC(B)                                                                                             \
+    k_qtb_spectra<B><<<blocks, SPEC_THREADS, sm, s->stream>>>(n_dof, N, ilog2(2 * N), s->qtb_dof_type, s->qtb_v, \
+                                                              s->qtb_F, s->qtb_tw2, s->qtb_part)
+    switch (spec_bpt(N)) {
+        case 1: QHP_SPEC(1); break;
+        case 2: QHP_SPEC(2); break;
+        case 3: QHP_SPEC(3); break;
+        case 5: QHP_SPEC(5); break;
+        default: QHP_SPEC(9); break;
+    }
+#undef QHP_SPEC
+    return cudaGetLastError();
+}
 
 int enqueue_filter(qhp_system_s* s) {
     const int N = s->n_seg;
@@ -310,8 +494,8 @@ int enqueue_filter(qhp_system_s* s) {
     const double wcut = s->th.omega_cut_cm > 0.0 ? s->th.omega_cut_cm * CM1 : INFINITY;
     k_qtb_sqrtS<<<(2 * (N + 1) + 127) / 128, 128, 0, s->stream>>>(N, s->th.dt_fs * 1e-3, kT, HBAR, s->th.gamma0,
                                                                   wcut, s->qtb_gamma, s->qtb_sqrtS);
-    k_qtb_taps<<<(4 * N + 127) / 128, 128, 0, s->stream>>>(N, s->qtb_sqrtS, s->qtb_h);
-    k_qtb_filter<<<(8 * N + 127) / 128, 128, 0, s->stream>>>(N, s->qtb_h, s->qtb_H);
+    k_qtb_taps<<<4 * N, TAP_THREADS, 0, s->stream>>>(N, s->qtb_sqrtS, s->qtb_h);
+    k_qtb_filter<<<8 * N, TAP_THREADS, 0, s->stream>>>(N, ilog2(4 * N), s->qtb_h, s->qtb_H);
     s->launches += 3;
     QHP_CUDA(cudaGetLastError());
     return QHP_OK;
@@ -321,7 +505,7 @@ int enqueue_generate(qhp_system_s* s, int64_t seg) {
     const int N = s->n_seg, n_dof = 3 * s->N;
     const int n_pairs = (n_dof + 1) / 2;
     const int grid = (n_pairs + GEN_PAIRS - 1) / GEN_PAIRS;
-    k_qtb_generate<<<grid, 256, gen_smem(N), s->stream>>>(n_dof, N, ilog2(4 * N), seg, s->seed, s->qtb_dof_type,
+    k_qtb_generate<<<grid, GEN_THREADS, gen_smem(N), s->stream>>>(n_dof, N, ilog2(4 * N), seg, s->seed, s->qtb_dof_type,
                                                           s->qtb_H, s->qtb_tw4, s->qtb_u);
     s->launches++;
     QHP_CUDA(cudaGetLastError());
@@ -373,7 +557,11 @@ int qtb_setup(qhp_system_s* s) {
         QHP_CUDA(cudaMemcpy(s->qtb_dof_type, dt_.data(), sizeof(int) * n_dof, cudaMemcpyHostToDevice));
         QHP_CUDA(cudaMemcpy(s->qtb_mdof, md.data(), sizeof(double) * n_dof, cudaMemcpyHostToDevice));
         QHP_CUDA(cudaFuncSetAttribute(k_qtb_generate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gen_smem(2048)));
-        QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
+        QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
+        QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
+        QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
+        QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
+        QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
     }
     std::vector<double> g(2 * (size_t)(N + 1), s->th.gamma0);
     QHP_CUDA(cudaMemcpy(s->qtb_gamma, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice));
@@ -392,17 +580,17 @@ int qtb_setup(qhp_system_s* s) {
 // Spectra of the finished segment, adaptation, filter and noise of the next segment.
 cudaError_t launch_qtb_segment_end(qhp_system_s* s) {
     const int N = s->n_seg, n_dof = 3 * s->N;
-    const int n_pairs = (n_dof + 1) / 2;
-    const int blocks = std::min(SPEC_BLOCKS, n_pairs);
-    k_qtb_spectra<<<blocks, 256, spec_smem(N), s->stream>>>(n_dof, N, ilog2(2 * N), s->th.dt_fs * 1e-3, s->qtb_dof_type,
-                                                            s->qtb_mdof, s->qtb_gamma, s->qtb_v, s->qtb_F, s->qtb_tw2,
-                                                            s->qtb_part);
+    const int blocks = spectra_blocks(s);
+    {
+        const cudaError_t e = launch_spectra(s, blocks);
+        if (e != cudaSuccess) return e;
+    }
     int nO = 0;
     for (int i = 0; i < s->N; ++i) nO += s->type[i] == 0;
     const double n_O = 3.0 * nO, n_H = 3.0 * (s->N - nO);
     const double wavg = exp(-N * s->th.dt_fs * 1e-3 / (s->th.tau_ratio_ps > 0 ? s->th.tau_ratio_ps : 1.0));
     k_qtb_adapt<<<(2 * (N + 1) + 127) / 128, 128, 0, s->stream>>>(
-        blocks, N, s->qtb_part, n_O, n_H, s->ff.m_O, s->ff.m_H, s->th.adapt, s->th.a_gamma,
+        blocks, N, s->th.dt_fs * 1e-3 / N, s->qtb_part, n_O, n_H, s->ff.m_O, s->ff.m_H, s->th.adapt, s->th.a_gamma,
         s->th.gamma_min_frac * s->th.gamma0, wavg, s->qtb_ratio_first, s->qtb_gamma, s->qtb_avg, s->qtb_delta);
     s->launches += 2;
     if (s->th.adapt == QHP_ADAPT_RATIO) s->qtb_ratio_first = 0;

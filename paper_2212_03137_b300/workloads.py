@@ -142,6 +142,10 @@ CONFIGS = {
     "adqtb_mixed_72000w": RunConfig(name="adqtb_mixed_72000w", n_mol=72000, box=129.0, rc=9.0, P=1,
                                     dt_fs=0.5, gamma0=20.0, thermostat="adqtb", precision="mixed",
                                     steps=10240, n_seg=1024, omega_cut_cm=15000.0, a_gamma=10.0),
+    # a smaller adQTB box of the same density and settings (profiling and parity sizes)
+    "adqtb_mixed_8000w": RunConfig(name="adqtb_mixed_8000w", n_mol=8000, box=box_edge_for(8000), rc=9.0, P=1,
+                                   dt_fs=0.5, gamma0=20.0, thermostat="adqtb", precision="mixed",
+                                   steps=2048, n_seg=1024, omega_cut_cm=15000.0, a_gamma=10.0),
     "grad_216w": RunConfig(name="grad_216w", n_mol=216, box=18.6, rc=9.0, P=16,
                            dt_fs=0.5, gamma0=1.0, precision="fp64", steps=200),
 }
