@@ -23,6 +23,8 @@ quantum effects", arXiv 2212.03137):
   adaptation (Sec. II.B Eqs. (12)-(15); Sec. III.B Eqs. (21)-(26));
 * ``philox``        - Philox4x32-10 (Salmon et al., SC'11) and Box-Muller,
   the random numbers both sides draw from the same counters;
+* ``respa``         - BAOAB-RESPA multiple time stepping and ring-polymer
+  contraction of the slow (nonbonded) forces (Sec. III.A.2, Eqs. (18)-(20));
 * ``gradients``     - dU_P/dx and dU_P/dtheta (analytic) for the force-field
   parameters theta = (eps, sigma, q_O, k_b, k_theta), and the gradient of a
   K-step trajectory average by central differences of whole trajectories.
