@@ -123,6 +123,18 @@ int qhp_set_beads(qhp_sys sys, int P, double temperature_K, uint64_t seed);
  * n_seg a power of two in [4, 2048]; the first noise segment is generated here. */
 int qhp_set_thermostat(qhp_sys sys, const qhp_thermo* th);
 
+/* Multiple time stepping with ring-polymer contraction (Sec. III.A.2, Eqs. (18)-(20)).
+ * V = V_s + V_f with V_f the bonded terms (on all P beads) and V_s the nonbonded ones,
+ * evaluated on contracted_beads beads: the Fourier interpolant of the contracted_beads
+ * lowest-frequency normal modes at equally spaced imaginary times (0 means P: no
+ * contraction).  With n_alt >= 1 each qhp_step_rpmd step is one outer step
+ * B_s(n dt/2) [B_f(dt/2) A O A B_f(dt/2)]^n B_s(n dt/2) of n_alt inner steps of the
+ * thermostat's dt (the step counter advances by n_alt); n_alt = 0 returns to plain BAOAB.
+ * Needs an initialised mixed-precision system with the PILE or NVE thermostat
+ * (QHP_ERR_STATE otherwise); contracted_beads must be a power of two dividing P.
+ * qhp_get_energy and qhp_get_forces keep their full-ring-polymer definitions. */
+int qhp_set_respa(qhp_sys sys, int n_alt, int contracted_beads);
+
 /* Advance n BAOAB steps (Eq. (17)) with the PILE thermostat, or with the adQTB
  * O step for qhp_step_adqtb.  Asynchronous; n >= 0. */
 int qhp_step_rpmd(qhp_sys sys, int n);

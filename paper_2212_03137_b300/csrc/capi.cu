@@ -45,6 +45,12 @@ void free_all(qhp_system_s* s) {
     s->qtb_dof_type = nullptr;
     s->n_seg = 0;
     s->grad = GradBuffers{};
+    s->respa_n = 0;   // RESPA buffers lived in the same pool
+    s->pc = 0;
+    s->Ffix_s = nullptr;
+    s->pos_c = nullptr;
+    s->fmode_s = nullptr;
+    s->Cmat_f = nullptr;
     s->nbr = nullptr;
     s->nbr_cap = 0;
 }
@@ -135,12 +141,33 @@ void invalidate_graph(qhp_system_s* s) {
 // Positions, list check (+ rebuild when due), forces, projection; no time step.
 int enqueue_forces(qhp_system_s* s, bool force_rebuild, bool energy) {
     QHP_CUDA(launch_integrate(s, false, false));
+    if (s->respa_n) QHP_CUDA(launch_contract(s, false));
     QHP_CUDA(launch_list_check(s, force_rebuild));
     QHP_CUDA(launch_rebuild(s));
     QHP_CUDA(launch_integrate_gated(s));
+    if (s->respa_n) QHP_CUDA(launch_contract(s, true));
     QHP_CUDA(launch_cover_check(s));
     QHP_CUDA(launch_forces(s, energy));
     QHP_CUDA(launch_project(s, false));
+    s->forces_kind = 0;
+    return QHP_OK;
+}
+
+// RESPA forces at the current modes, no kick: fast (bonded, all beads) into fmode and
+// slow (nonbonded, contracted beads) into fmode_s.
+int enqueue_respa_forces(qhp_system_s* s, bool force_rebuild) {
+    QHP_CUDA(launch_integrate(s, false, false));
+    QHP_CUDA(launch_contract(s, false));
+    QHP_CUDA(launch_list_check(s, force_rebuild));
+    QHP_CUDA(launch_rebuild(s));
+    QHP_CUDA(launch_integrate_gated(s));
+    QHP_CUDA(launch_contract(s, true));
+    QHP_CUDA(launch_cover_check(s));
+    QHP_CUDA(launch_bonded_fast(s));
+    QHP_CUDA(launch_project(s, false));
+    QHP_CUDA(launch_pair_contracted(s));
+    QHP_CUDA(launch_project_contracted(s, false));
+    s->forces_kind = 1;
     return QHP_OK;
 }
 
@@ -171,6 +198,7 @@ int enqueue_rebuild_conditional(qhp_system_s* s) {
     const int64_t before = s->launches;
     cudaError_t e = launch_rebuild(s);
     if (e == cudaSuccess) e = launch_integrate_gated(s);
+    if (e == cudaSuccess && s->respa_n) e = launch_contract(s, true);
     if (e == cudaSuccess) e = launch_cover_check(s);
     s->kernels_per_rebuild = s->launches - before;
     s->stream = main;
@@ -219,7 +247,46 @@ int capture_step_graph(qhp_system_s* s, bool adqtb) {
     return QHP_OK;
 }
 
+// One RESPA outer step (Sec. III.A.2): B_s(n dt/2) [B_f A O A B_f]^n B_s(n dt/2).  The
+// first inner integrate applies B_s together with B_f; the list is checked once, right
+// before the slow forces, on the displacements of all inner steps and the contracted beads.
+// Stage timestamps: inner steps | list | slow pair forces | last bonded | projections.
+int enqueue_respa_step(qhp_system_s* s) {
+    const bool prof = s->prof_on != 0;
+    const int n = s->respa_n;
+    if (prof) QHP_CUDA(record_stage(s, 0));
+    for (int i = 0; i < n; ++i) {
+        QHP_CUDA(launch_integrate_respa(s, i == 0 ? (double)n : 0.0));
+        if (i < n - 1) {
+            QHP_CUDA(launch_bonded_fast(s));
+            QHP_CUDA(launch_project(s, true));
+            continue;
+        }
+        QHP_CUDA(launch_contract(s, false));
+        if (prof) QHP_CUDA(record_stage(s, 1));
+        QHP_CUDA(launch_list_check(s, false));
+        if (s->cond_active) {
+            TRY(enqueue_rebuild_conditional(s));
+        } else {
+            QHP_CUDA(launch_rebuild(s));
+            QHP_CUDA(launch_integrate_gated(s));
+            QHP_CUDA(launch_contract(s, true));
+            QHP_CUDA(launch_cover_check(s));
+        }
+        if (prof) QHP_CUDA(record_stage(s, 2));
+        QHP_CUDA(launch_pair_contracted(s));
+        if (prof) QHP_CUDA(record_stage(s, 3));
+        QHP_CUDA(launch_bonded_fast(s));
+        if (prof) QHP_CUDA(record_stage(s, 4));
+        QHP_CUDA(launch_project(s, true));
+        QHP_CUDA(launch_project_contracted(s, true));
+        if (prof) QHP_CUDA(record_stage(s, 5));
+    }
+    return QHP_OK;
+}
+
 int enqueue_step(qhp_system_s* s, bool adqtb) {
+    if (s->respa_n && !adqtb) return enqueue_respa_step(s);
     // Under capture the stage records become event-record nodes, so every replay
     // timestamps its stages.
     const bool prof = s->prof_on != 0;
@@ -303,17 +370,20 @@ int run_steps(qhp_system_s* s, int n, bool adqtb) {
     }
     // report a fault found by earlier asynchronous work, without waiting for it
     if (s->status_event && cudaEventQuery(s->status_event) == cudaSuccess) TRY(check_status(s, *s->status_host));
-    if (!s->forces_valid) {
-        TRY(enqueue_forces(s, !s->list_valid, false));
+    const int want = s->respa_n ? 1 : 0;
+    if (!s->forces_valid || s->forces_kind != want) {
+        if (want) TRY(enqueue_respa_forces(s, !s->list_valid));
+        else TRY(enqueue_forces(s, !s->list_valid, false));
         s->forces_valid = true;
         s->list_valid = true;
     }
     if (n == 0) return QHP_OK;
     const int kind = adqtb ? 1 : 0;
+    const int inner = s->respa_n ? s->respa_n : 1;   // time steps per call unit
     if (!s->use_graphs) {
         for (int k = 0; k < n; ++k) {
             TRY(enqueue_step(s, adqtb));
-            s->step += 1;
+            s->step += inner;
             if (adqtb && s->step % s->n_seg == 0) TRY(enqueue_segment_end(s, s->step));
         }
         return post_status(s);
@@ -336,7 +406,7 @@ int run_steps(qhp_system_s* s, int n, bool adqtb) {
     } else {
         TRY(enqueue_step(s, adqtb));
     }
-    s->step += n;
+    s->step += (int64_t)n * inner;
     return post_status(s);
 }
 
@@ -615,6 +685,64 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     TRY(ensure_capacity(s));
     if (s->th.kind == QHP_THERMO_ADQTB) TRY(qtb_setup(s));
     return sync_and_check(s);
+}
+
+int qhp_set_respa(qhp_sys s, int n_alt, int contracted_beads) {
+    if (!s || !s->beads_set) {
+        set_error("qhp_set_respa: system not initialised");
+        return QHP_ERR_STATE;
+    }
+    if (n_alt < 0 || n_alt > 1024) {
+        set_error("qhp_set_respa: n_alt must be in [0, 1024] (0 turns RESPA off)");
+        return QHP_ERR_ARG;
+    }
+    if (n_alt == 0) {
+        if (s->respa_n) {
+            s->respa_n = 0;
+            s->forces_valid = false;
+            invalidate_graph(s);
+        }
+        return QHP_OK;
+    }
+    if (s->precision != QHP_MIXED || s->th.kind == QHP_THERMO_ADQTB) {
+        set_error("qhp_set_respa: needs a mixed-precision system with the PILE or NVE thermostat");
+        return QHP_ERR_STATE;
+    }
+    const int P = s->P;
+    const int pc = contracted_beads == 0 ? P : contracted_beads;
+    if (pc < 1 || pc > P || (pc & (pc - 1)) || P % pc) {
+        set_error("qhp_set_respa: contracted beads must be a power of two dividing P");
+        return QHP_ERR_ARG;
+    }
+    if (pc != s->pc || !s->Ffix_s) {
+        TRY(dalloc(s, &s->Ffix_s, (size_t)s->N * 3 * pc));
+        TRY(dalloc(s, &s->pos_c, (size_t)s->N * pc));
+        if (!s->fmode_s) TRY(dalloc(s, &s->fmode_s, (size_t)s->N * 3 * P));
+        TRY(dalloc(s, &s->Cmat_f, (size_t)pc * P));
+        // C[b][n] = sqrt(P) T[b P/pc][n] on the pc lowest-frequency modes (centroid, cos/sin of
+        // frequencies 1 .. pc/2 - 1, cos of frequency pc/2), 0 on the others (Eq. (20))
+        std::vector<double> T;
+        transfer_matrix_host(P, T);
+        std::vector<char> keep(P, 0);
+        keep[0] = 1;
+        if (pc == P) {
+            std::fill(keep.begin(), keep.end(), 1);
+        } else {
+            for (int k = 1; k < pc / 2; ++k) keep[k] = keep[P - k] = 1;
+            if (pc >= 2) keep[pc / 2] = 1;
+        }
+        std::vector<float> C((size_t)pc * P, 0.0f);
+        for (int b = 0; b < pc; ++b)
+            for (int n = 0; n < P; ++n)
+                if (keep[n]) C[(size_t)b * P + n] = (float)(sqrt((double)P) * T[(size_t)(b * (P / pc)) * P + n]);
+        for (int b = 0; b < pc; ++b) C[(size_t)b * P] = 1.0f;   // the centroid enters every bead with weight one
+        QHP_CUDA(cudaMemcpy(s->Cmat_f, C.data(), sizeof(float) * C.size(), cudaMemcpyHostToDevice));
+    }
+    s->respa_n = n_alt;
+    s->pc = pc;
+    s->forces_valid = false;
+    invalidate_graph(s);
+    return QHP_OK;
 }
 
 int qhp_set_thermostat(qhp_sys s, const qhp_thermo* th) {

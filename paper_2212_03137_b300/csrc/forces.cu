@@ -372,6 +372,7 @@ struct BondArgs {
     double* Fd;
     double* ebond;
     BondConsts c;
+    int overwrite;   // mixed: store the bonded forces instead of adding them to the pair forces
 };
 
 template <bool MIXED, bool ENERGY>
@@ -414,9 +415,15 @@ __device__ __forceinline__ void bonded_body(const BondArgs& A, int t) {
             const float f1 = pb1 * d1[d] + pa * (d2[d] * ir12 - cs * d1[d] / (r1 * r1));
             const float f2 = pb2 * d2[d] + pa * (d1[d] * ir12 - cs * d2[d] / (r2 * r2));
             const long long i1 = __float2ll_rn(f1 * FIX_SCALE_F), i2 = __float2ll_rn(f2 * FIX_SCALE_F);
-            Ffix[((size_t)aH1 * 3 + d) * P + b] += i1;
-            Ffix[((size_t)aH2 * 3 + d) * P + b] += i2;
-            Ffix[((size_t)aO * 3 + d) * P + b] -= i1 + i2;
+            if (A.overwrite) {
+                Ffix[((size_t)aH1 * 3 + d) * P + b] = i1;
+                Ffix[((size_t)aH2 * 3 + d) * P + b] = i2;
+                Ffix[((size_t)aO * 3 + d) * P + b] = -(i1 + i2);
+            } else {
+                Ffix[((size_t)aH1 * 3 + d) * P + b] += i1;
+                Ffix[((size_t)aH2 * 3 + d) * P + b] += i2;
+                Ffix[((size_t)aO * 3 + d) * P + b] -= i1 + i2;
+            }
         }
         if (ENERGY)
             ebond[t] = 0.5 * c.kb * ((double)(r1 - r0) * (r1 - r0) + (double)(r2 - r0) * (r2 - r0)) +
@@ -603,6 +610,7 @@ BondArgs make_bond_args(const qhp_system_s* s) {
     B.Fd = s->Fd;
     B.ebond = s->e_bond;
     B.c = BondConsts{s->ff.k_b, s->ff.r0, s->ff.k_theta, s->ff.theta0, s->L};
+    B.overwrite = 0;
     return B;
 }
 
@@ -754,6 +762,37 @@ cudaError_t launch_forces(qhp_system_s* s, bool energy) {
         if (e != cudaSuccess) return e;
     }
     return launch_bonded(s, energy);
+}
+
+// RESPA: the bonded (fast) forces alone into the fixed-point bead forces.
+cudaError_t launch_bonded_fast(qhp_system_s* s) {
+    BondArgs B = make_bond_args(s);
+    B.overwrite = 1;
+    const int g2 = (s->n_mol * s->P + 127) / 128;
+    k_bonded<true, false><<<g2, 128, 0, s->stream>>>(B);
+    s->launches += 1;
+    return cudaGetLastError();
+}
+
+// RESPA with contraction: the nonbonded (slow) forces on the Pc contracted beads.
+cudaError_t launch_pair_contracted(qhp_system_s* s) {
+    PairArgs A = make_pair_args(s);
+    A.P = s->pc;
+    A.W = s->pair_w > 0 ? s->pair_w : pair_warps_default(s->pc);
+    A.pos = s->pos_c;
+    A.F = s->Ffix_s;
+    switch (s->pc) {
+        case 1: pair_mixed_dispatch<1>(A, false, s->stream); break;
+        case 2: pair_mixed_dispatch<2>(A, false, s->stream); break;
+        case 4: pair_mixed_dispatch<4>(A, false, s->stream); break;
+        case 8: pair_mixed_dispatch<8>(A, false, s->stream); break;
+        case 16: pair_mixed_dispatch<16>(A, false, s->stream); break;
+        case 32: pair_mixed_dispatch<32>(A, false, s->stream); break;
+        case 64: pair_mixed_dispatch<64>(A, false, s->stream); break;
+        default: return cudaErrorInvalidValue;
+    }
+    s->launches += 1;
+    return cudaGetLastError();
 }
 
 // In-cutoff bead pairs (each unordered pair once) and how many of them are O-O.

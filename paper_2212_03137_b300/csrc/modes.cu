@@ -36,6 +36,8 @@ struct IntegrateArgs {
     const float* qtb_u;
     float *qtb_v, *qtb_F;
     const int* gate;       // if set, the kernel runs only when *gate != 0
+    const double* fmode_s; // RESPA: slow mode forces kicked together with the fast ones
+    double ws;             //        with weight ws (n_alt on the first inner step, else 0)
 };
 
 __device__ __forceinline__ void block_max_atomic(float v, unsigned* out) {
@@ -97,7 +99,9 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
         if (INTEGRATE) {
             const double* c = A.tab + ((size_t)A.type[a] * P + n) * MT_N;
             const unsigned long long step = *A.step_ctr;
-            pm += A.half_dt_acc * A.fmode[idx];                       // B
+            double f = A.fmode[idx];
+            if (A.fmode_s) f += A.ws * A.fmode_s[idx];                // RESPA: B_s(n dt/2) B_f(dt/2)
+            pm += A.half_dt_acc * f;                                  // B
             free_half(n, c, q, pm);                                   // A
             if (ADQTB) {                                              // O with colored noise
                 const int dof = a * 3 + d;
@@ -322,6 +326,60 @@ __global__ void k_beads_fp64(int N, int P, const double* Q, const double* Tm, do
     out[((size_t)b * N + dof / 3) * 3 + dof % 3] = acc;
 }
 
+// Ring-polymer contraction (Sec. III.A.2, Eq. (20)): positions of the Pc contracted beads,
+// xc_b = sum_n C[b][n] Q_n with C[b][0] = 1, as FP32 offsets from the atom's anchor
+// (FP64 centroid offset + FP32 fluctuation sum, as for the full beads), one thread per
+// (atom, contracted bead); their deviations enter the list's displacement maximum.
+__global__ void __launch_bounds__(128) k_contract(int N, int P, int Pc, const double* __restrict__ Q,
+                                                  const float* __restrict__ Cf, const double* __restrict__ anchor,
+                                                  const int* __restrict__ iperm, float4* __restrict__ pos_c,
+                                                  unsigned* dev_max, const int* gate) {
+    if (gate && !*gate) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    float dv = 0.0f;
+    if (t < N * Pc) {
+        const int a = t / Pc, b = t % Pc;
+        float x[3];
+        for (int d = 0; d < 3; ++d) {
+            const double* q = Q + ((size_t)a * 3 + d) * P;
+            float fl = 0.0f;
+            for (int n = 1; n < P; ++n) fl = fmaf(Cf[b * P + n], (float)q[n], fl);
+            x[d] = (float)(q[0] - anchor[a * 3 + d]) + fl;
+        }
+        pos_c[(size_t)iperm[a] * Pc + b] = make_float4(x[0], x[1], x[2], 0.0f);
+        dv = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    }
+    for (int o = 16; o > 0; o >>= 1) dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dev_max, __float_as_uint(dv));
+}
+
+// Slow mode forces of the contracted ring polymer, f_n = (1/Pc) sum_b C[b][n] F_b (Eq. (20)),
+// f_0 the exact integer sum of the fixed-point forces; with a kick, P_n += scale f_n.
+__global__ void k_project_contracted(int N, int P, int Pc, const long long* __restrict__ Fs,
+                                     const float* __restrict__ Cf, double* __restrict__ fmode_s, double* Pm,
+                                     double kick_scale, unsigned* status) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * 3 * P) return;
+    const int n = idx % P, dof = idx / P;
+    const long long* F = Fs + (size_t)dof * Pc;
+    double f;
+    if (n == 0) {
+        long long sum = 0;
+        for (int b = 0; b < Pc; ++b) sum += F[b];
+        f = (double)sum * (1.0 / (FIX_SCALE * (double)Pc));   // Pc is a power of two: exact scaling
+    } else {
+        float acc = 0.0f;
+        for (int b = 0; b < Pc; ++b) acc = fmaf(Cf[b * P + n], __ll2float_rn(F[b]) * (1.0f / FIX_SCALE_F), acc);
+        f = (double)acc / (double)Pc;
+    }
+    fmode_s[idx] = f;
+    if (Pm) {
+        const double p = Pm[idx] + kick_scale * f;
+        Pm[idx] = p;
+        if (!isfinite(p)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
 size_t integrate_smem(int P, bool mixed) { return BLOCK * 16 + (size_t)P * P * (mixed ? 4 : 8); }
 
 }  // namespace
@@ -407,6 +465,8 @@ static IntegrateArgs make_iargs(qhp_system_s* s) {
     A.qtb_v = s->qtb_v;
     A.qtb_F = s->qtb_F;
     A.gate = nullptr;
+    A.fmode_s = nullptr;
+    A.ws = 0.0;
     return A;
 }
 
@@ -524,6 +584,34 @@ cudaError_t launch_init_modes(qhp_system_s* s) {
     // the initial positions are staged in the anchor buffer by the caller
     k_init_modes<<<(total + 255) / 256, 256, 0, s->stream>>>(s->N, s->P, s->seed, KB * s->temperature * ACC,
                                                              s->anchor, s->mass, omega_d, s->Q, s->Pm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_respa(qhp_system_s* s, double ws) {
+    IntegrateArgs A = make_iargs(s);
+    A.fmode_s = s->fmode_s;
+    A.ws = ws;
+    const int grid = (s->N + A.apb - 1) / A.apb;
+    s->launches++;
+    k_integrate<true, false, true><<<grid, BLOCK, integrate_smem(s->P, true), s->stream>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract(qhp_system_s* s, bool gated) {
+    const int total = s->N * s->pc;
+    s->launches++;
+    k_contract<<<(total + 127) / 128, 128, 0, s->stream>>>(s->N, s->P, s->pc, s->Q, s->Cmat_f, s->anchor, s->iperm,
+                                                           s->pos_c, s->dev_max, gated ? s->rebuild_flag : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_contracted(qhp_system_s* s, bool kick) {
+    const int total = s->N * 3 * s->P;
+    const double scale = kick ? s->respa_n * 0.5 * s->th.dt_fs * 1e-3 * ACC : 0.0;
+    s->launches++;
+    k_project_contracted<<<(total + 255) / 256, 256, 0, s->stream>>>(s->N, s->P, s->pc, s->Ffix_s, s->Cmat_f,
+                                                                     s->fmode_s, kick ? s->Pm : nullptr, scale,
+                                                                     s->status);
     return cudaGetLastError();
 }
 

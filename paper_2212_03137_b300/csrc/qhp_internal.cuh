@@ -190,6 +190,15 @@ struct qhp_system_s {
     int64_t rebuilds_host = 0;
     int keep_anchor = 0;           // 1 while a checkpoint restore rebuilds from stored anchors
     int pair_w = 0;                // warps per atom of the mixed pair kernel (0: default for P)
+    // RESPA (Sec. III.A.2): n inner steps per outer step; slow (nonbonded) forces on pc
+    // contracted beads; fast (bonded) forces in Ffix / fmode
+    int respa_n = 0;               // 0: plain BAOAB
+    int pc = 0;
+    long long* Ffix_s = nullptr;   // [N][3][pc] slow bead forces (fixed point)
+    float4* pos_c = nullptr;       // [sorted N][pc] contracted positions (offsets from anchors)
+    double* fmode_s = nullptr;     // [N][3][P] slow mode forces
+    float* Cmat_f = nullptr;       // [pc][P] contraction matrix
+    int forces_kind = 0;           // what fmode holds: 0 full forces, 1 RESPA fast + slow
     int prof_on = 0;               // per-stage events recorded inside each step
     int use_graphs = 1;            // 0: launch each step's kernels directly
     cudaGraphConditionalHandle cond_handle = 0;   // IF node around the rebuild chain of the step graph
@@ -296,6 +305,11 @@ cudaError_t launch_project(qhp_system_s* s, bool kick);
 cudaError_t launch_list_check(qhp_system_s* s, bool force);
 cudaError_t launch_rebuild(qhp_system_s* s);
 cudaError_t launch_cover_check(qhp_system_s* s);   // after a rebuild: every bead within skin/2
+cudaError_t launch_integrate_respa(qhp_system_s* s, double ws);   // B (fast + ws x slow) A O A
+cudaError_t launch_contract(qhp_system_s* s, bool gated);        // contracted bead positions
+cudaError_t launch_project_contracted(qhp_system_s* s, bool kick);
+cudaError_t launch_bonded_fast(qhp_system_s* s);
+cudaError_t launch_pair_contracted(qhp_system_s* s);
 cudaError_t launch_forces(qhp_system_s* s, bool energy);
 cudaError_t launch_pair(qhp_system_s* s, bool energy);
 cudaError_t launch_bonded(qhp_system_s* s, bool energy);

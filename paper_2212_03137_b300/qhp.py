@@ -87,6 +87,7 @@ _SIGS = {
     "qhp_set_stream": [_VP, _VP],
     "qhp_set_profiling": [_VP, C.c_int],
     "qhp_set_graph_mode": [_VP, C.c_int],
+    "qhp_set_respa": [_VP, C.c_int, C.c_int],
     "qhp_get_profile": [_VP, _VP],
     "qhp_count_pairs": [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "qhp_estimators_noalloc": [C.c_int, C.c_int, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP],
@@ -330,6 +331,10 @@ def qhp_set_stream(h, stream_ptr: int | None) -> None:
 
 def qhp_set_profiling(h, on: bool) -> None:
     _check(lib().qhp_set_profiling(h, 1 if on else 0))
+
+
+def qhp_set_respa(h, n_alt: int, contracted_beads: int = 0) -> None:
+    _check(lib().qhp_set_respa(h, int(n_alt), int(contracted_beads)))
 
 
 def qhp_set_graph_mode(h, use_graphs: bool) -> None:

@@ -142,6 +142,11 @@ CONFIGS = {
     "adqtb_mixed_72000w": RunConfig(name="adqtb_mixed_72000w", n_mol=72000, box=129.0, rc=9.0, P=1,
                                     dt_fs=0.5, gamma0=20.0, thermostat="adqtb", precision="mixed",
                                     steps=10240, n_seg=1024, omega_cut_cm=15000.0, a_gamma=10.0),
+    # the 4,096-water RPMD box with BAOAB-RESPA (4 inner steps of 0.5 fs per 2 fs outer step)
+    # and the nonbonded forces on 8 contracted beads (Sec. III.A.2)
+    "rpmd_respa_rpc_4096w": RunConfig(name="rpmd_respa_rpc_4096w", n_mol=4096, box=49.7, rc=9.0, P=32,
+                                      dt_fs=0.5, gamma0=1.0, precision="mixed", steps=1000,
+                                      extra={"respa": 4, "contracted_beads": 8}),
     # a smaller adQTB box of the same density and settings (profiling and parity sizes)
     "adqtb_mixed_8000w": RunConfig(name="adqtb_mixed_8000w", n_mol=8000, box=box_edge_for(8000), rc=9.0, P=1,
                                    dt_fs=0.5, gamma0=20.0, thermostat="adqtb", precision="mixed",
