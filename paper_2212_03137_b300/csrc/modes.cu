@@ -52,6 +52,35 @@ __device__ __forceinline__ void block_max_atomic(float v, unsigned* out) {
     }
 }
 
+// Dot products over the P modes / beads with four independent partial sums (the chains of
+// dependent FMAs are what limits these short loops).
+__device__ __forceinline__ float dot4(const float* __restrict__ a, int sa, const float* __restrict__ b, int k0,
+                                      int k1) {
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+        s0 = fmaf(a[k * sa], b[k], s0);
+        s1 = fmaf(a[(k + 1) * sa], b[k + 1], s1);
+        s2 = fmaf(a[(k + 2) * sa], b[k + 2], s2);
+        s3 = fmaf(a[(k + 3) * sa], b[k + 3], s3);
+    }
+    for (; k < k1; ++k) s0 = fmaf(a[k * sa], b[k], s0);
+    return (s0 + s1) + (s2 + s3);
+}
+__device__ __forceinline__ double dot4(const double* __restrict__ a, int sa, const double* __restrict__ b, int k0,
+                                       int k1) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+        s0 = fma(a[k * sa], b[k], s0);
+        s1 = fma(a[(k + 1) * sa], b[k + 1], s1);
+        s2 = fma(a[(k + 2) * sa], b[k + 2], s2);
+        s3 = fma(a[(k + 3) * sa], b[k + 3], s3);
+    }
+    for (; k < k1; ++k) s0 = fma(a[k * sa], b[k], s0);
+    return (s0 + s1) + (s2 + s3);
+}
+
 // Exact free flow over dt/2 (Eq. (9) without forces): drift for the centroid, the
 // three-shear form of the rotation for n > 0 (determinant one whatever the rounding).
 __device__ __forceinline__ void free_half(int n, const double* c, double& q, double& pm) {
@@ -136,11 +165,11 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
             // FP32 pair kernel, where 1e-7 relative on sub-Angstrom fluctuations is far
             // below the pair arithmetic's own rounding.
             float acc = 0.0f;
-            for (int k = 1; k < P; ++k) acc = fmaf(Tsf[k * P + n], qf[base + k], acc);
+            acc = dot4(Tsf + n, P, qf + base, 1, P);
             xr[t] = (float)(qs[base] - anc) + acc;
         } else {
             double acc = 0.0;
-            for (int k = 0; k < P; ++k) acc = fma(Tsd[k * P + n], qs[base + k], acc);
+            acc = dot4(Tsd + n, P, qs + base, 0, P);
             A.pos_d[((size_t)d * A.N + s) * P + n] = acc;
             xr[t] = (float)(acc - anc);
         }
@@ -156,11 +185,17 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
     block_max_atomic(dv, A.dev_max);
 }
 
+// Persistent grid: a block walks atom groups blockIdx.x, + gridDim.x, ... and stages the
+// transform in shared memory once.
 template <bool MIXED, bool ADQTB, bool INTEGRATE>
 __global__ void __launch_bounds__(BLOCK) k_integrate(const __grid_constant__ IntegrateArgs A) {
     extern __shared__ unsigned char smem_raw[];
     if (A.gate && !*A.gate) return;                                   // uniform over the grid
-    integrate_body<MIXED, ADQTB, INTEGRATE>(A, blockIdx.x, smem_raw, true);
+    const int nb = (A.N + A.apb - 1) / A.apb;
+    for (int bx = blockIdx.x; bx < nb; bx += gridDim.x) {
+        if (bx != (int)blockIdx.x) __syncthreads();                    // previous group done with smem
+        integrate_body<MIXED, ADQTB, INTEGRATE>(A, bx, smem_raw, bx == (int)blockIdx.x);
+    }
 }
 
 // Batched systems: a persistent grid, each block walking its contiguous range of
@@ -230,12 +265,12 @@ __device__ __forceinline__ void project_body(const ProjectArgs& A, int bx, unsig
                 f = (double)sum * (1.0 / (FIX_SCALE * (double)P));   // power of two: exact scaling
             } else {
                 float acc = 0.0f;
-                for (int b = 0; b < P; ++b) acc = fmaf(Tsf[b * P + n], Ff[base + b], acc);
+                acc = dot4(Tsf + n, P, Ff + base, 0, P);
                 f = (double)acc;
             }
         } else {
             double acc = 0.0;
-            for (int b = 0; b < P; ++b) acc = fma(Tsd[b * P + n], Fs[base + b], acc);
+            acc = dot4(Tsd + n, P, Fs + base, 0, P);
             f = acc;
         }
         A.fmode[idx] = f;
@@ -251,7 +286,11 @@ __device__ __forceinline__ void project_body(const ProjectArgs& A, int bx, unsig
 template <bool MIXED, bool KICK>
 __global__ void __launch_bounds__(BLOCK) k_project(const __grid_constant__ ProjectArgs A) {
     extern __shared__ unsigned char smem_raw[];
-    project_body<MIXED, KICK>(A, blockIdx.x, smem_raw, true);
+    const int nb = (A.N + A.apb - 1) / A.apb;
+    for (int bx = blockIdx.x; bx < nb; bx += gridDim.x) {
+        if (bx != (int)blockIdx.x) __syncthreads();
+        project_body<MIXED, KICK>(A, bx, smem_raw, bx == (int)blockIdx.x);
+    }
 }
 
 __global__ void __launch_bounds__(BLOCK) k_project_batch(const ProjectArgs* __restrict__ args,
@@ -342,9 +381,14 @@ __global__ void __launch_bounds__(128) k_contract(int N, int P, int Pc, const do
         float x[3];
         for (int d = 0; d < 3; ++d) {
             const double* q = Q + ((size_t)a * 3 + d) * P;
-            float fl = 0.0f;
-            for (int n = 1; n < P; ++n) fl = fmaf(Cf[b * P + n], (float)q[n], fl);
-            x[d] = (float)(q[0] - anchor[a * 3 + d]) + fl;
+            float f0 = 0.0f, f1 = 0.0f;
+            int n = 1;
+            for (; n + 1 < P; n += 2) {
+                f0 = fmaf(Cf[b * P + n], (float)q[n], f0);
+                f1 = fmaf(Cf[b * P + n + 1], (float)q[n + 1], f1);
+            }
+            if (n < P) f0 = fmaf(Cf[b * P + n], (float)q[n], f0);
+            x[d] = (float)(q[0] - anchor[a * 3 + d]) + (f0 + f1);
         }
         pos_c[(size_t)iperm[a] * Pc + b] = make_float4(x[0], x[1], x[2], 0.0f);
         dv = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
@@ -355,22 +399,41 @@ __global__ void __launch_bounds__(128) k_contract(int N, int P, int Pc, const do
 
 // Slow mode forces of the contracted ring polymer, f_n = (1/Pc) sum_b C[b][n] F_b (Eq. (20)),
 // f_0 the exact integer sum of the fixed-point forces; with a kick, P_n += scale f_n.
+// A warp covers whole dofs (P a power of two): lane b of a dof's first lanes converts its
+// bead force b once and the others read it by shuffle.
 __global__ void k_project_contracted(int N, int P, int Pc, const long long* __restrict__ Fs,
                                      const float* __restrict__ Cf, double* __restrict__ fmode_s, double* Pm,
                                      double kick_scale, unsigned* status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= N * 3 * P) return;
+    const int total = N * 3 * P;
+    const bool valid = idx < total;
     const int n = idx % P, dof = idx / P;
-    const long long* F = Fs + (size_t)dof * Pc;
+    const int lane = threadIdx.x & 31;
+    const long long* F = Fs + (size_t)(valid ? dof : 0) * Pc;
+    float s0 = 0.0f, s1 = 0.0f;
+    if (Pc <= 32) {   // uniform over the grid
+        // the dof's bead forces are converted once, by the lanes sub = 0 .. Pc-1 of the warp
+        // (P >= 32: a warp holds one dof; P < 32: a group of P lanes per dof)
+        const int l0 = P >= 32 ? 0 : lane - n;
+        const int sub = P >= 32 ? lane : n;
+        const float mine = (valid && sub < Pc) ? __ll2float_rn(F[sub]) * (1.0f / FIX_SCALE_F) : 0.0f;
+        for (int b = 0; b < Pc; b += 2) {
+            const float f0 = __shfl_sync(0xffffffffu, mine, l0 + b);
+            const float f1 = __shfl_sync(0xffffffffu, mine, l0 + (b + 1 < Pc ? b + 1 : b));
+            s0 = fmaf(Cf[b * P + n], f0, s0);
+            if (b + 1 < Pc) s1 = fmaf(Cf[(b + 1) * P + n], f1, s1);
+        }
+    } else if (valid) {
+        for (int b = 0; b < Pc; ++b) s0 = fmaf(Cf[b * P + n], __ll2float_rn(F[b]) * (1.0f / FIX_SCALE_F), s0);
+    }
+    if (!valid) return;
     double f;
     if (n == 0) {
         long long sum = 0;
         for (int b = 0; b < Pc; ++b) sum += F[b];
         f = (double)sum * (1.0 / (FIX_SCALE * (double)Pc));   // Pc is a power of two: exact scaling
     } else {
-        float acc = 0.0f;
-        for (int b = 0; b < Pc; ++b) acc = fmaf(Cf[b * P + n], __ll2float_rn(F[b]) * (1.0f / FIX_SCALE_F), acc);
-        f = (double)acc / (double)Pc;
+        f = (double)(s0 + s1) / (double)Pc;
     }
     fmode_s[idx] = f;
     if (Pm) {
@@ -438,6 +501,14 @@ void mode_constants(qhp_system_s* s) {
     }
 }
 
+// Persistent grid size: resident blocks of 192 threads on every SM (at most the work).
+static int persistent_grid(const void* kernel, size_t smem, int work_blocks) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BLOCK, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return std::max(1, std::min(work_blocks, per_sm * sm_count()));
+}
+
 static IntegrateArgs make_iargs(qhp_system_s* s) {
     IntegrateArgs A;
     A.N = s->N;
@@ -473,30 +544,41 @@ static IntegrateArgs make_iargs(qhp_system_s* s) {
 cudaError_t launch_integrate_gated(qhp_system_s* s) {
     IntegrateArgs A = make_iargs(s);
     A.gate = s->rebuild_flag;
-    const int grid = (s->N + A.apb - 1) / A.apb;
+    const int nb = (s->N + A.apb - 1) / A.apb;
     const bool mixed = s->precision == QHP_MIXED;
     const size_t sm = integrate_smem(s->P, mixed);
     s->launches++;
-    if (mixed) k_integrate<true, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
-    else k_integrate<false, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+    if (mixed) {
+        const int grid = persistent_grid((const void*)k_integrate<true, false, false>, sm, nb);
+        k_integrate<true, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+    } else {
+        const int grid = persistent_grid((const void*)k_integrate<false, false, false>, sm, nb);
+        k_integrate<false, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_integrate(qhp_system_s* s, bool integrate, bool adqtb) {
     IntegrateArgs A = make_iargs(s);
-    const int grid = (s->N + A.apb - 1) / A.apb;
+    const int nb = (s->N + A.apb - 1) / A.apb;
     const bool mixed = s->precision == QHP_MIXED;
     const size_t sm = integrate_smem(s->P, mixed);
     s->launches++;
+#define QHP_INT(M, Q, I)                                                                     \
+    do {                                                                                     \
+        const int grid = persistent_grid((const void*)k_integrate<M, Q, I>, sm, nb);        \
+        k_integrate<M, Q, I><<<grid, BLOCK, sm, s->stream>>>(A);                            \
+    } while (0)
     if (mixed) {
-        if (!integrate) k_integrate<true, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
-        else if (adqtb) k_integrate<true, true, true><<<grid, BLOCK, sm, s->stream>>>(A);
-        else k_integrate<true, false, true><<<grid, BLOCK, sm, s->stream>>>(A);
+        if (!integrate) QHP_INT(true, false, false);
+        else if (adqtb) QHP_INT(true, true, true);
+        else QHP_INT(true, false, true);
     } else {
-        if (!integrate) k_integrate<false, false, false><<<grid, BLOCK, sm, s->stream>>>(A);
-        else if (adqtb) k_integrate<false, true, true><<<grid, BLOCK, sm, s->stream>>>(A);
-        else k_integrate<false, false, true><<<grid, BLOCK, sm, s->stream>>>(A);
+        if (!integrate) QHP_INT(false, false, false);
+        else if (adqtb) QHP_INT(false, true, true);
+        else QHP_INT(false, false, true);
     }
+#undef QHP_INT
     return cudaGetLastError();
 }
 
@@ -519,17 +601,23 @@ static ProjectArgs make_pargs(qhp_system_s* s) {
 
 cudaError_t launch_project(qhp_system_s* s, bool kick) {
     const ProjectArgs A = make_pargs(s);
-    const int grid = (s->N + A.apb - 1) / A.apb;
+    const int nb = (s->N + A.apb - 1) / A.apb;
     const bool mixed = s->precision == QHP_MIXED;
     const size_t sm = (size_t)s->P * s->P * (mixed ? 4 : 8);
     s->launches++;
+#define QHP_PRJ(M, K)                                                                        \
+    do {                                                                                     \
+        const int grid = persistent_grid((const void*)k_project<M, K>, sm, nb);             \
+        k_project<M, K><<<grid, BLOCK, sm, s->stream>>>(A);                                 \
+    } while (0)
     if (mixed) {
-        if (kick) k_project<true, true><<<grid, BLOCK, sm, s->stream>>>(A);
-        else k_project<true, false><<<grid, BLOCK, sm, s->stream>>>(A);
+        if (kick) QHP_PRJ(true, true);
+        else QHP_PRJ(true, false);
     } else {
-        if (kick) k_project<false, true><<<grid, BLOCK, sm, s->stream>>>(A);
-        else k_project<false, false><<<grid, BLOCK, sm, s->stream>>>(A);
+        if (kick) QHP_PRJ(false, true);
+        else QHP_PRJ(false, false);
     }
+#undef QHP_PRJ
     return cudaGetLastError();
 }
 
@@ -591,9 +679,11 @@ cudaError_t launch_integrate_respa(qhp_system_s* s, double ws) {
     IntegrateArgs A = make_iargs(s);
     A.fmode_s = s->fmode_s;
     A.ws = ws;
-    const int grid = (s->N + A.apb - 1) / A.apb;
+    const int nb = (s->N + A.apb - 1) / A.apb;
+    const size_t sm = integrate_smem(s->P, true);
+    const int grid = persistent_grid((const void*)k_integrate<true, false, true>, sm, nb);
     s->launches++;
-    k_integrate<true, false, true><<<grid, BLOCK, integrate_smem(s->P, true), s->stream>>>(A);
+    k_integrate<true, false, true><<<grid, BLOCK, sm, s->stream>>>(A);
     return cudaGetLastError();
 }
 

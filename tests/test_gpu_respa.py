@@ -35,10 +35,11 @@ def _oracle_run(cfg, n_alt, Pc, n_outer):
     return st
 
 
-@pytest.mark.parametrize("n_alt,Pc", [(4, 4), (2, 1), (3, 8)], ids=["n4_Pc4", "n2_centroid", "n3_full"])
-def test_respa_contraction_trajectory_matches_oracle(n_alt, Pc):
-    cfg = SMALL
-    n_outer = 4
+@pytest.mark.parametrize("P,n_alt,Pc", [(8, 4, 4), (8, 2, 1), (8, 3, 8), (64, 2, 16), (4, 2, 2)],
+                         ids=["P8_n4_Pc4", "P8_n2_centroid", "P8_n3_full", "P64_n2_Pc16", "P4_n2_Pc2"])
+def test_respa_contraction_trajectory_matches_oracle(P, n_alt, Pc):
+    cfg = small_mixed_config(512, P=P)
+    n_outer = 4 if P <= 8 else 2
     st = _oracle_run(cfg, n_alt, Pc, n_outer)
     with qhp.System.from_config(cfg) as s:
         qhp.qhp_set_respa(s.h, n_alt, Pc)
