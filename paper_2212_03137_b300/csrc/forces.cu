@@ -249,8 +249,18 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, float* red_
     }
 }
 
+// Residency: with P = 16 or 32 (one atom per block, lanes = beads) the loop is latency bound
+// and 16 resident blocks (64 warps, 32 registers a thread) measured 12% faster than 10-12;
+// with few beads the compiler's default allocation (minimum 0) is faster, and P = 64 (two
+// beads a lane) would spill.  The batched kernel, which carries every variant of its P,
+// keeps 12 blocks.
+template <int P>
+__host__ __device__ constexpr int pair_min_blocks() { return (P == 16 || P == 32) ? 16 : 0; }
+template <int P>
+__host__ __device__ constexpr int pair_batch_min_blocks() { return (P == 16 || P == 32) ? 12 : 0; }
+
 template <int P, int W, bool ALL, bool ENERGY>
-__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(const __grid_constant__ PairArgs A) {
+__global__ void __launch_bounds__(32 * PAIR_WARPS, pair_min_blocks<P>()) k_pair_mixed(const __grid_constant__ PairArgs A) {
     __shared__ float red[PAIR_RED];
     pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, red);
 }
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_mixed(const __grid_con
 // specialisation (uniform over the block).  One launch per P keeps every launch at the
 // registers of its own bead count.
 template <int P>
-__global__ void __launch_bounds__(32 * PAIR_WARPS) k_pair_batch(const PairArgs* __restrict__ args,
+__global__ void __launch_bounds__(32 * PAIR_WARPS, pair_batch_min_blocks<P>()) k_pair_batch(const PairArgs* __restrict__ args,
                                                                 const int2* __restrict__ items,
                                                                 const int* __restrict__ ranges) {
     __shared__ float red[PAIR_RED];
