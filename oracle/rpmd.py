@@ -33,6 +33,7 @@ class Params:
     gamma0: float          # ps^-1
     seed: int
     hbar: float = HBAR
+    integrator: str = "baoab"   # "baoab" (exact A) or "bcocb" (Cayley A, Sec. III.A.1)
 
     @property
     def kT(self) -> float:
@@ -114,6 +115,11 @@ def free_flow(state: State, prm: Params, masses: np.ndarray, tau: float) -> None
     w = prm.omegas()
     Q, Pm = state.Q.copy(), state.Pm.copy()
     Q[:, :, 0] = state.Q[:, :, 0] + state.Pm[:, :, 0] * tau / m
+    if prm.integrator == "bcocb":
+        for n in range(1, prm.P):
+            Q[:, :, n], Pm[:, :, n] = cayley_flow(state.Q[:, :, n], state.Pm[:, :, n], m, w[n], tau)
+        state.Q, state.Pm = Q, Pm
+        return
     for n in range(1, prm.P):
         th = w[n] * tau
         a = np.tan(0.5 * th) / (m * w[n])
@@ -123,6 +129,16 @@ def free_flow(state: State, prm: Params, masses: np.ndarray, tau: float) -> None
         Q[:, :, n] = q + a * p
         Pm[:, :, n] = p
     state.Q, state.Pm = Q, Pm
+
+
+def cayley_flow(q, p, m, w: float, h: float):
+    """C: the Cayley transform of the free ring-polymer flow of one mode over h (the BCOCB
+    scheme of Sec. III.A.1, after Korol et al.): with A = [[0, 1/m], [-m w^2, 0]],
+    cay(hA) = (I - hA/2)^{-1} (I + hA/2), written out:
+        q' = ((1 - u) q + (h/m) p) / (1 + u),  p' = (-h m w^2 q + (1 - u) p) / (1 + u),  u = (h w/2)^2."""
+    u = (0.5 * h * w) ** 2
+    d = 1.0 + u
+    return ((1.0 - u) * q + (h / m) * p) / d, (-h * m * w * w * q + (1.0 - u) * p) / d
 
 
 def ou(state: State, prm: Params, masses: np.ndarray, dt: float, noise: np.ndarray | None = None) -> None:
