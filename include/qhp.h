@@ -47,6 +47,7 @@ enum {
 enum { QHP_FP64 = 0, QHP_MIXED = 1 };
 enum { QHP_THERMO_PILE = 0, QHP_THERMO_ADQTB = 1, QHP_THERMO_NVE = 2 };
 enum { QHP_ADAPT_NONE = 0, QHP_ADAPT_SIMPLE = 1, QHP_ADAPT_RATIO = 2 };
+enum { QHP_INTEGRATOR_BAOAB = 0, QHP_INTEGRATOR_BCOCB = 1 };
 
 /* Interatomic potential V (the paper is independent of V; this is a flexible
  * q-SPC/Fw-style water): O-O Lennard-Jones shifted to 0 at rc, damped-shifted-
@@ -67,7 +68,11 @@ typedef struct {
  * adapted per atom type at every segment end (adapt = QHP_ADAPT_*, rate
  * a_gamma in ps^-1 per kcal/mol, RATIO time tau_ratio_ps) and clamped at
  * gamma_min_frac * gamma0.  NVE: no friction and no noise on any mode (the
- * ring-polymer equations of motion, Eq. (9), integrated as B A A B). */
+ * ring-polymer equations of motion, Eq. (9), integrated as B A A B).
+ * integrator: QHP_INTEGRATOR_BAOAB (exact free ring-polymer flow A) or
+ * QHP_INTEGRATOR_BCOCB (Sec. III.A.1: A(dt/2) of every internal mode replaced by its
+ * Cayley transform, a rotation by 2 atan(omega dt/4) instead of omega dt/2, stable for
+ * any omega dt). */
 typedef struct {
     int kind;
     double gamma0;        /* ps^-1 */
@@ -78,6 +83,7 @@ typedef struct {
     double gamma_min_frac;
     int adapt;
     double tau_ratio_ps;
+    int integrator;
 } qhp_thermo;
 
 /* Estimators at the current state (kcal/mol).

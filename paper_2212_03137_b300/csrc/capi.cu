@@ -751,8 +751,9 @@ int qhp_set_thermostat(qhp_sys s, const qhp_thermo* th) {
         return QHP_ERR_ARG;
     }
     if (!(th->dt_fs > 0.0) || th->gamma0 < 0.0 ||
-        (th->kind != QHP_THERMO_PILE && th->kind != QHP_THERMO_ADQTB && th->kind != QHP_THERMO_NVE)) {
-        set_error("thermostat: need dt_fs > 0, gamma0 >= 0, kind PILE, ADQTB or NVE");
+        (th->kind != QHP_THERMO_PILE && th->kind != QHP_THERMO_ADQTB && th->kind != QHP_THERMO_NVE) ||
+        (th->integrator != QHP_INTEGRATOR_BAOAB && th->integrator != QHP_INTEGRATOR_BCOCB)) {
+        set_error("thermostat: need dt_fs > 0, gamma0 >= 0, kind PILE, ADQTB or NVE, integrator BAOAB or BCOCB");
         return QHP_ERR_ARG;
     }
     if (th->kind == QHP_THERMO_ADQTB) {

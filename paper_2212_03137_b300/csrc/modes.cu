@@ -476,7 +476,10 @@ void mode_constants(qhp_system_s* s) {
         }
         const double w = 2.0 * P * kT / HBAR * sin(pi * n / P);
         m.omega[n] = w;
-        const double th = w * 0.5 * dt;
+        // A(dt/2) is the rotation by th = w dt/2 (BAOAB) or, for BCOCB, the Cayley transform,
+        // the rotation by 2 atan(th/2); either is applied as the same three shears
+        double th = w * 0.5 * dt;
+        if (s->th.integrator == QHP_INTEGRATOR_BCOCB) th = 2.0 * atan(0.5 * th);
         m.shear_a[n] = (n == 0) ? 0.0 : tan(0.5 * th) / w;
         m.shear_b[n] = (n == 0) ? 0.0 : sin(th) * w;
         double g = (n == 0) ? s->th.gamma0 : fmax(s->th.gamma0, w);

@@ -22,6 +22,7 @@ ERRORS = {-1: "QHP_ERR_ARG", -2: "QHP_ERR_CUDA", -3: "QHP_ERR_TIMEOUT", -4: "QHP
 QHP_FP64, QHP_MIXED = 0, 1
 QHP_THERMO_PILE, QHP_THERMO_ADQTB, QHP_THERMO_NVE = 0, 1, 2
 QHP_ADAPT_NONE, QHP_ADAPT_SIMPLE, QHP_ADAPT_RATIO = 0, 1, 2
+QHP_INTEGRATOR_BAOAB, QHP_INTEGRATOR_BCOCB = 0, 1
 
 
 class QHPError(RuntimeError):
@@ -38,7 +39,7 @@ class qhp_ff(C.Structure):
 class qhp_thermo(C.Structure):
     _fields_ = [("kind", C.c_int), ("gamma0", C.c_double), ("dt_fs", C.c_double), ("n_seg", C.c_int),
                 ("omega_cut_cm", C.c_double), ("a_gamma", C.c_double), ("gamma_min_frac", C.c_double),
-                ("adapt", C.c_int), ("tau_ratio_ps", C.c_double)]
+                ("adapt", C.c_int), ("tau_ratio_ps", C.c_double), ("integrator", C.c_int)]
 
 
 class qhp_energy(C.Structure):
@@ -506,8 +507,10 @@ def make_ff(rc: float, skin: float = 2.0, **kw) -> qhp_ff:
 
 def make_thermo(kind: int = QHP_THERMO_PILE, gamma0: float = 1.0, dt_fs: float = 0.5, n_seg: int = 1024,
                 omega_cut_cm: float = 15000.0, a_gamma: float = 10.0, gamma_min_frac: float = 0.01,
-                adapt: int = QHP_ADAPT_SIMPLE, tau_ratio_ps: float = 1.0) -> qhp_thermo:
-    return qhp_thermo(kind, gamma0, dt_fs, n_seg, omega_cut_cm, a_gamma, gamma_min_frac, adapt, tau_ratio_ps)
+                adapt: int = QHP_ADAPT_SIMPLE, tau_ratio_ps: float = 1.0,
+                integrator: int = QHP_INTEGRATOR_BAOAB) -> qhp_thermo:
+    return qhp_thermo(kind, gamma0, dt_fs, n_seg, omega_cut_cm, a_gamma, gamma_min_frac, adapt, tau_ratio_ps,
+                      integrator)
 
 
 class System:
@@ -541,7 +544,9 @@ class System:
         prec = {"fp64": QHP_FP64, "mixed": QHP_MIXED}[precision or cfg.precision]
         kind = QHP_THERMO_ADQTB if cfg.thermostat == "adqtb" else QHP_THERMO_PILE
         th = make_thermo(kind=kind, gamma0=cfg.gamma0, dt_fs=cfg.dt_fs, n_seg=cfg.n_seg,
-                         omega_cut_cm=cfg.omega_cut_cm, a_gamma=cfg.a_gamma, gamma_min_frac=cfg.gamma_min_frac)
+                         omega_cut_cm=cfg.omega_cut_cm, a_gamma=cfg.a_gamma, gamma_min_frac=cfg.gamma_min_frac,
+                         integrator=QHP_INTEGRATOR_BCOCB if cfg.extra.get("integrator") == "bcocb"
+                         else QHP_INTEGRATOR_BAOAB)
         return cls(w.box, w.types, w.molecule, w.pos, prec, make_ff(cfg.rc, cfg.skin), cfg.P, cfg.temperature,
                    over.get("seed", cfg.seed), th)
 
