@@ -233,6 +233,21 @@ int qhp_energy_grad(qhp_sys sys, double* energy, double* dE_dx, double* dE_dthet
 int qhp_energy_grad_device(qhp_sys sys, const double* x, double* energy, double* dE_dx, double* dE_dtheta);
 int qhp_segment_grad(qhp_sys sys, int K, int block, int observable, double* J, double* dJ_dtheta);
 
+/* Free-energy differences by path-integral BAR (Sec. IV, Eqs. (27)-(28), appendix A).
+ * qhp_state_energies: at the current beads, out[4] = {U_P(A), U_P(B), V_A(x_0), V_B(x_0)}:
+ * the bead-averaged potential (Eq. (3)) and the potential of bead 0 alone, for the two
+ * parameter sets theta_A, theta_B = (eps, sigma, q_O, k_b, k_theta) (q_H = -q_O/2; the
+ * other terms as set by qhp_set_forcefield).  FP64, synchronous.
+ * qhp_bar: Dlt F_AB = F_B - F_A (kcal/mol) from dU = U_B - U_A sampled in state A
+ * (dU_A[n_A]) and in state B (dU_B[n_B]) (host arrays), beta in (kcal/mol)^-1: the
+ * self-consistent solution of Eqs. (27)-(28), iterated from C = ln(n_B/n_A)/beta until C
+ * moves by less than tol (QHP_ERR_STATE after 10000 iterations).  Pass bead-averaged
+ * differences for PI-BAR or single-bead ones for the single-bead estimator.  The paper's
+ * hydration free energies need solute parameters and are not reproduced. */
+int qhp_state_energies(qhp_sys sys, const double* theta_A, const double* theta_B, double* out);
+int qhp_bar(const double* dU_A, int n_A, const double* dU_B, int n_B, double beta, double tol, double* dF,
+            int* iterations);
+
 /* Batched systems (the paper's bead parallelism extended to many independent systems;
  * no counterpart in the paper).  A batch steps n_sys initialised mixed-precision systems
  * with the PILE or NVE thermostat together: each step is one CUDA graph of batched

@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqhp.so")
-SOURCES = ["capi.cu", "modes.cu", "neighbor.cu", "forces.cu", "qtb.cu", "noalloc.cu", "inspect.cu", "grad.cu", "batch.cu"]
+SOURCES = ["capi.cu", "modes.cu", "neighbor.cu", "forces.cu", "qtb.cu", "noalloc.cu", "inspect.cu", "grad.cu", "batch.cu", "bar.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

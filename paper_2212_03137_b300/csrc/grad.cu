@@ -404,8 +404,15 @@ int grad_prepare(qhp_system_s* s, int qbuf_steps) {
     return QHP_OK;
 }
 
-GradConsts grad_consts(const qhp_system_s* s) {
-    const qhp_ff& f = s->ff;
+GradConsts grad_consts(const qhp_system_s* s, const double* theta = nullptr) {
+    qhp_ff f = s->ff;
+    if (theta) {   // another parameter set (eps, sigma, q_O, k_b, k_theta) on the same system
+        f.eps = theta[0];
+        f.sigma = theta[1];
+        f.q_O = theta[2];
+        f.k_b = theta[3];
+        f.k_theta = theta[4];
+    }
     GradConsts c;
     const double rc = f.rc, a = f.alpha;
     c.L = s->L;
@@ -440,12 +447,27 @@ double self_coef(const qhp_system_s* s) {
 
 inline int blocks(int64_t n, int tb) { return (int)((n + tb - 1) / tb); }
 
+// out[0] = sum over rows b, b + stride, ... of column col (one bead's rows of a partial array)
+__global__ void k_colsum_stride(const double* __restrict__ in, int rows, int stride, int cols, int col,
+                                double* __restrict__ out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int r = threadIdx.x * stride; r < rows; r += 256 * stride) s += in[(size_t)r * cols + col];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
 // Pair + bonded terms at the configuration in g.x (Pk beads; with tangent g.v when dual),
 // then the column sums of both partial arrays into g.sums[0..13].
 cudaError_t eval_terms(qhp_system_s* s, int Pk, bool dual, const double* x, const double* v, double* F, double* Ft,
-                       double* part, double* partb) {
+                       double* part, double* partb, const double* theta = nullptr) {
     GradBuffers& g = s->grad;
-    const GradConsts c = grad_consts(s);
+    const GradConsts c = grad_consts(s, theta);
     const int N = s->N;
     const int warps = N * Pk;
     if (dual)
@@ -588,6 +610,42 @@ int qhp_energy_grad(qhp_sys s, double* energy, double* dE_dx, double* dE_dtheta)
     }
     TRY(qhp_energy_grad_device(s, nullptr, energy, dev, dE_dtheta));
     if (dE_dx) QHP_CUDA(cudaMemcpy(dE_dx, dev, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return QHP_OK;
+}
+
+int qhp_state_energies(qhp_sys s, const double* theta_A, const double* theta_B, double* out) {
+    if (!s || !s->beads_set || !theta_A || !theta_B || !out) {
+        set_error("qhp_state_energies: need an initialised system and two parameter sets");
+        return QHP_ERR_ARG;
+    }
+    TRY(grad_prepare(s, 0));
+    GradBuffers& g = s->grad;
+    const int N = s->N, P = s->P;
+    const int64_t n = (int64_t)N * 3 * P;
+    if (!s->list_valid) TRY(rebuild_list_now(s));   // after a step the list covers the beads
+    k_modes_to_x<<<blocks(n, 256), 256, 0, s->stream>>>(N, P, s->Q, s->Tmat, s->iperm, g.x);
+    s->launches++;
+    const double sc = self_coef(s);
+    const double* th[2] = {theta_A, theta_B};
+    double h[2][4];
+    for (int k = 0; k < 2; ++k) {
+        QHP_CUDA(eval_terms(s, P, false, g.x, nullptr, g.F, nullptr, g.part, g.partb, th[k]));
+        // bead 0 alone: rows w = i P + 0 of the pair partials, t = m P + 0 of the bonded ones
+        k_colsum_stride<<<1, 256, 0, s->stream>>>(g.part, N * P, P, 2 * NPART, 0, g.sums + 16);
+        k_colsum_stride<<<1, 256, 0, s->stream>>>(g.partb, s->n_mol * P, P, 2 * NPARTB, 0, g.sums + 17);
+        s->launches += 2;
+        QHP_CUDA(cudaGetLastError());
+        double r[18];
+        QHP_CUDA(cudaMemcpyAsync(r, g.sums, sizeof r, cudaMemcpyDeviceToHost, s->stream));
+        QHP_CUDA(cudaStreamSynchronize(s->stream));
+        const double qO = th[k][2];
+        h[k][0] = (r[0] + r[2 * NPART]) / P + sc * qO * qO;   // U_P (Eq. (3))
+        h[k][1] = r[16] + r[17] + sc * qO * qO;               // V(x_0)
+    }
+    out[0] = h[0][0];
+    out[1] = h[1][0];
+    out[2] = h[0][1];
+    out[3] = h[1][1];
     return QHP_OK;
 }
 

@@ -103,6 +103,8 @@ _SIGS = {
     "qhp_batch_get_profile": [_VP, _VP],
     "qhp_autotune": [_VP, C.c_int, _IP],
     "qhp_set_pair_warps": [_VP, C.c_int],
+    "qhp_state_energies": [_VP, _DP, _DP, _DP],
+    "qhp_bar": [_DP, C.c_int, _DP, C.c_int, C.c_double, C.c_double, _DP, _IP],
     "qhp_energy_grad": [_VP, _DP, _DP, _DP],
     "qhp_energy_grad_device": [_VP, _VP, _DP, _VP, _DP],
     "qhp_segment_grad": [_VP, C.c_int, C.c_int, C.c_int, _DP, _DP],
@@ -482,6 +484,25 @@ def qhp_segment_grad(h, K: int, block: int, observable: int):
     g = np.empty(5)
     _check(lib().qhp_segment_grad(h, int(K), int(block), int(observable), C.byref(J), _dp(g)))
     return J.value, g
+
+
+def qhp_state_energies(h, theta_A, theta_B) -> np.ndarray:
+    """[U_P(A), U_P(B), V_A(x_0), V_B(x_0)] at the current beads (kcal/mol)."""
+    a = np.ascontiguousarray(theta_A, dtype=np.float64)
+    b = np.ascontiguousarray(theta_B, dtype=np.float64)
+    out = np.empty(4)
+    _check(lib().qhp_state_energies(h, _dp(a), _dp(b), _dp(out)))
+    return out
+
+
+def qhp_bar(dU_A, dU_B, beta: float, tol: float = 1e-12):
+    """(Dlt F_AB, iterations) by (PI-)BAR from dU = U_B - U_A sampled in A and in B."""
+    a = np.ascontiguousarray(dU_A, dtype=np.float64)
+    b = np.ascontiguousarray(dU_B, dtype=np.float64)
+    dF = C.c_double(0.0)
+    it = C.c_int(0)
+    _check(lib().qhp_bar(_dp(a), len(a), _dp(b), len(b), float(beta), float(tol), C.byref(dF), C.byref(it)))
+    return dF.value, it.value
 
 
 def ff_with_params(ff: qhp_ff, theta) -> qhp_ff:
