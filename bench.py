@@ -42,6 +42,17 @@ FLOPS_PAIR = 45
 FLOPS_LJ = 8
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over all ranks of the initialised process group (the job's time is
+    its slowest rank's), followed by a barrier."""
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    td.barrier()
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -199,11 +210,7 @@ def run_ours(args, ws, rank, local):
         seg = {"segment_end_step_ms": end_ms, "segment_work_ms": extra, "n_seg": cfg.n_seg,
                "amortised_ms_per_step": extra / cfg.n_seg, "timed_segment_ends": len(ends)}
     if dist:
-        import torch.distributed as td
-        t = torch.tensor([total_ms], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        total_ms = float(t.item())
-        td.barrier()
+        total_ms = max_over_ranks(total_ms, dev)
     qhp.qhp_set_profiling(h, False)
 
     units = N * P * args.steps * inner * ws
@@ -314,11 +321,7 @@ def run_batch(args, ws, rank, local):
     i1 = qhp.qhp_batch_get_info(b.h)
     total_ms = float(np.sum(step_ms))
     if dist:
-        import torch.distributed as td
-        t = torch.tensor([total_ms], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        total_ms = float(t.item())
-        td.barrier()
+        total_ms = max_over_ranks(total_ms, dev)
     value = units_step * args.steps * ws / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
     out = None
