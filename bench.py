@@ -33,6 +33,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# load every kernel of the library at start-up: the first replay of a rarely taken
+# conditional branch (a list rebuild) must not pay for lazy module loading in a timed step
+os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
 
 METRIC = "atom·bead·steps/s (ns/day) RPMD & adQTB water vs FP64 GPU path at stated error"
 UNIT = "atom·bead·steps/s"
@@ -258,7 +261,7 @@ def run_ours(args, ws, rank, local):
         if seg is not None:
             out["adqtb_segment"] = seg
     if args.e2e:
-        e2e = _e2e(args, h, N, P, step, dev, ws)
+        e2e = _e2e(args, h, N, P, step, dev, ws, inner)
         if rank == 0:
             out["e2e"] = e2e
     if args.fp64 and rank == 0:
@@ -358,26 +361,29 @@ def run_batch(args, ws, rank, local):
             "list_rebuilds": int(i1.rebuilds - i0.rebuilds),
         }
     if args.e2e:
-        # public API with host buffers: every box's momenta uploaded from pinned memory,
-        # one batched step, every box's centroids read back
+        # public API with host buffers: every box's momenta live on the host between steps
+        # (uploaded from pinned memory, one batched step, read back) and every box's
+        # centroids are read back as the result
         import torch as _t
         pins = [_t.from_numpy(qhp.qhp_get_modes(s.h)[1]).pin_memory() for s in systems]
+        ptrs = [qhp.C.cast(p.data_ptr(), qhp._DP) for p in pins]
         cents = [np.empty((s.n_atoms, 3)) for s in systems]
         n = max(1, min(args.steps, 20))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(n):
-            for s, pin in zip(systems, pins):
-                qhp.lib().qhp_set_modes(s.h, None, qhp.C.cast(pin.data_ptr(), qhp._DP))
+            for s, ptr in zip(systems, ptrs):
+                qhp.lib().qhp_set_modes(s.h, None, ptr)
             b.step(1)
-            for s, c in zip(systems, cents):
+            for s, ptr, c in zip(systems, ptrs, cents):
+                qhp.lib().qhp_get_modes(s.h, None, ptr)
                 qhp.lib().qhp_get_centroid(s.h, c.ctypes.data_as(qhp._DP))
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
         if rank == 0:
             out["e2e"] = {"value": units_step * n * ws / dt, "unit": UNIT,
                           "h2d_bytes_per_step": int(sum(p.numel() * 8 for p in pins)),
-                          "d2h_bytes_per_step": int(sum(c.nbytes for c in cents))}
+                          "d2h_bytes_per_step": int(sum(p.numel() * 8 for p in pins) + sum(c.nbytes for c in cents))}
     b.close()
     for s in systems:
         s.close()
@@ -395,24 +401,28 @@ def run_batch(args, ws, rank, local):
     return out
 
 
-def _e2e(args, h, N, P, step, dev, ws):
-    """Public API with host buffers: per step upload the momenta (pinned), step, read back the centroids."""
+def _e2e(args, h, N, P, step, dev, ws, inner=1):
+    """Public API with host buffers: the state's momenta live on the host between steps.  Per
+    step: upload them (pinned), step, read the new momenta back and the centroids (the
+    result).  The round trip keeps the dynamics exact (positions stay on the device)."""
     import torch
     from paper_2212_03137_b300 import qhp
     Q, Pm = qhp.qhp_get_modes(h)
     pin = torch.from_numpy(Pm).pin_memory()
     cent = np.empty((N, 3))
+    ptr = qhp.C.cast(pin.data_ptr(), qhp._DP)
     n = max(1, args.steps)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(n):
-        qhp.lib().qhp_set_modes(h, None, qhp.C.cast(pin.data_ptr(), qhp._DP))
+        qhp.lib().qhp_set_modes(h, None, ptr)
         step(h, 1)
+        qhp.lib().qhp_get_modes(h, None, ptr)
         qhp.lib().qhp_get_centroid(h, cent.ctypes.data_as(qhp._DP))
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
-    return {"value": N * P * n * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(Pm.nbytes),
-            "d2h_bytes_per_step": int(cent.nbytes)}
+    return {"value": N * P * n * inner * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(Pm.nbytes),
+            "d2h_bytes_per_step": int(Pm.nbytes + cent.nbytes)}
 
 
 def _fp64_path(args, cfg, dev):
