@@ -226,12 +226,17 @@ __global__ void k_sorted_attrs(const int* flag, int N, double L, const int* perm
 
 // Centroid Verlet list, one block per cell: the 125 stencil cells' candidates are staged
 // in shared memory (in stencil order, ascending index within a cell, i.e. the same order as
-// the per-atom scan) and every atom of the cell tests them from there.
-constexpr int LC_THREADS = 128;
+// the oracle's per-atom scan) and every atom of the cell tests them from there.  FILL = false
+// counts (set-up), true writes the rows.  A warp tests 32 candidates at a time; the accepted
+// ones go to a per-warp queue and entries are written 32 at a time from the queue, so the
+// separation arithmetic runs on full warps (a quarter of the candidates are accepted).
+constexpr int LC_THREADS = 256;
+constexpr int LC_WARPS = LC_THREADS / 32;
+constexpr int LC_MAXA = 8;     // atoms per warp in one pass over the staged candidates
 constexpr int LC_CHUNK = 768;   // 3 x 768 x 16 B of staged candidates: within the 48 KB static limit
 
 template <bool FILL>
-__global__ void __launch_bounds__(LC_THREADS) k_list_cells(
+__global__ void __launch_bounds__(LC_THREADS, 4) k_list_cells(
     const int* flag, int N, double L, int n_c, double r2max, float lo2, float hi2, const int* perm,
     const int* cell_start, const float4* cw, const float4* cwl, const int* mol_s, const int* type_s,
     const double* anchor, int* count, const int* start, int4* nbr, int row_cap, unsigned* status) {
@@ -240,7 +245,9 @@ __global__ void __launch_bounds__(LC_THREADS) k_list_cells(
     __shared__ float c_sx[125], c_sy[125], c_sz[125];
     __shared__ float4 s_w[LC_CHUNK];     // shifted wrapped centroid (prefilter), .w = mol as int bits
     __shared__ float4 s_l[LC_CHUNK];     // low parts, .w = j | H bit as int bits
-    __shared__ float4 s_s[LC_CHUNK];     // unshifted wrapped centroid (hi), .w = periodic shift code
+    __shared__ float4 s_s[LC_CHUNK];     // unshifted wrapped centroid (hi), .w = stencil cell as int bits
+    __shared__ int s_q[LC_WARPS][32];    // per-warp queue of accepted candidates
+    __shared__ int s_cnt[LC_WARPS][LC_MAXA];   // row lengths so far of the warp's atoms
     const int c = blockIdx.x;
     const int i0 = cell_start[c], i1 = cell_start[c + 1];
     if (i0 == i1) return;
@@ -274,56 +281,70 @@ __global__ void __launch_bounds__(LC_THREADS) k_list_cells(
     __syncthreads();
     const int M = c_off[125];
     const int lane = t & 31, w = t >> 5;
-    // per-warp state for up to ceil(atoms in cell / 4) atoms is kept across chunks
-    constexpr int MAXA = 16;   // atoms per warp handled in one pass; more are done in further passes
-    for (int ib = i0; ib < i1; ib += 4 * MAXA) {
-        int cnt[MAXA];
-#pragma unroll
-        for (int a = 0; a < MAXA; ++a) cnt[a] = 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int ib = i0; ib < i1; ib += LC_WARPS * LC_MAXA) {
+        if (lane < LC_MAXA) s_cnt[w][lane] = 0;
         for (int m0 = 0; m0 < M; m0 += LC_CHUNK) {
             const int mc = min(LC_CHUNK, M - m0);
             __syncthreads();
             for (int e = t; e < mc; e += LC_THREADS) {
                 const int m = m0 + e;
-                int k = 0;   // stencil cell of candidate m (binary search over 125 offsets)
-                int lo = 0, hi = 124;
+                int lo = 0, hi = 124;   // stencil cell of candidate m (binary search over 125 offsets)
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (c_off[mid] <= m) lo = mid;
                     else hi = mid - 1;
                 }
-                k = lo;
+                const int k = lo;
                 const int j = c_beg[k] + (m - c_off[k]);
                 const float4 wj = cw[j];
                 const float4 lj = cwl[j];
-                const float sx = c_sx[k], sy = c_sy[k], sz = c_sz[k];
-                s_w[e] = make_float4(wj.x + sx, wj.y + sy, wj.z + sz, __int_as_float(mol_s[j]));
+                s_w[e] = make_float4(wj.x + c_sx[k], wj.y + c_sy[k], wj.z + c_sz[k], __int_as_float(mol_s[j]));
                 s_l[e] = make_float4(lj.x, lj.y, lj.z, __int_as_float(j | (type_s[j] ? (int)0x80000000u : 0)));
-                const int code = (sx > 0.f ? 2 : (sx < 0.f ? 0 : 1)) + 3 * (sy > 0.f ? 2 : (sy < 0.f ? 0 : 1)) +
-                                 9 * (sz > 0.f ? 2 : (sz < 0.f ? 0 : 1));
-                s_s[e] = make_float4(wj.x, wj.y, wj.z, __int_as_float(code));
+                s_s[e] = make_float4(wj.x, wj.y, wj.z, __int_as_float(k));
             }
             __syncthreads();
-#pragma unroll
-            for (int a = 0; a < MAXA; ++a) {
-                const int i = ib + w + 4 * a;
+            for (int a = 0; a < LC_MAXA; ++a) {
+                const int i = ib + w + LC_WARPS * a;
                 if (i >= i1) break;
                 const float4 wi = cw[i];
                 const int mi = mol_s[i];
                 const int ai = perm[i];
-                int base = 0, lim = 0;
+                __syncwarp();
+                int cnt = s_cnt[w][a];
+                int base = 0, lim = 0, qn = 0;
                 float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (FILL) {
-                    base = start[i] + cnt[a];
+                    base = start[i] + cnt;
                     lim = start[i] + row_cap;
                     li = cwl[i];
                 }
+                // write the first n queued candidates as entries base .. base + n - 1
+                auto flush = [&](int n) {
+                    __syncwarp();
+                    if (lane < n) {
+                        const int e = s_q[w][lane];
+                        const int pos = base + lane;
+                        if (pos < lim) {
+                            const float4 sl = s_l[e];
+                            const float4 wj = s_s[e];
+                            const int k = __float_as_int(wj.w);
+                            const float kx = c_sx[k], ky = c_sy[k], kz = c_sz[k];
+                            const float Dx = sep_df(wj.x, sl.x, wi.x, li.x, kx, kx > 0.f ? Llo : (kx < 0.f ? -Llo : 0.f));
+                            const float Dy = sep_df(wj.y, sl.y, wi.y, li.y, ky, ky > 0.f ? Llo : (ky < 0.f ? -Llo : 0.f));
+                            const float Dz = sep_df(wj.z, sl.z, wi.z, li.z, kz, kz > 0.f ? Llo : (kz < 0.f ? -Llo : 0.f));
+                            nbr[pos] = make_int4(__float_as_int(sl.w), __float_as_int(Dx), __float_as_int(Dy),
+                                                 __float_as_int(Dz));
+                        }
+                    }
+                    base += n;
+                    __syncwarp();
+                };
                 for (int eb = 0; eb < mc; eb += 32) {
                     const int e = eb + lane;
                     bool acc = false;
-                    float4 sw = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (e < mc) {
-                        sw = s_w[e];
+                        const float4 sw = s_w[e];
                         if (__float_as_int(sw.w) != mi) {
                             const float ddx = sw.x - wi.x, ddy = sw.y - wi.y, ddz = sw.z - wi.z;
                             const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
@@ -342,36 +363,34 @@ __global__ void __launch_bounds__(LC_THREADS) k_list_cells(
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, acc);
-                    if (FILL && acc) {
-                        const int pos = base + __popc(bal & ((1u << lane) - 1u));
-                        if (pos < lim) {
-                            const float4 sl = s_l[e];
-                            const float4 wj = s_s[e];
-                            const int code = __float_as_int(wj.w);
-                            const float kx = (float)(code % 3 - 1), ky = (float)((code / 3) % 3 - 1),
-                                        kz = (float)(code / 9 - 1);
-                            const float Dx = sep_df(wj.x, sl.x, wi.x, li.x, kx * Lf, kx * Llo);
-                            const float Dy = sep_df(wj.y, sl.y, wi.y, li.y, ky * Lf, ky * Llo);
-                            const float Dz = sep_df(wj.z, sl.z, wi.z, li.z, kz * Lf, kz * Llo);
-                            nbr[pos] = make_int4(__float_as_int(sl.w), __float_as_int(Dx), __float_as_int(Dy),
-                                                 __float_as_int(Dz));
+                    const int nacc = __popc(bal);
+                    if (FILL) {
+                        if (qn + nacc > 32) {   // make room: write the queue first
+                            flush(qn);
+                            qn = 0;
+                        }
+                        if (acc) s_q[w][qn + __popc(bal & lt_mask)] = e;
+                        qn += nacc;
+                        if (qn == 32) {
+                            flush(32);
+                            qn = 0;
                         }
                     }
-                    const int nacc = __popc(bal);
-                    base += nacc;
-                    cnt[a] += nacc;
+                    cnt += nacc;
                 }
+                if (FILL && qn > 0) flush(qn);   // the staged candidates are replaced by the next chunk
+                __syncwarp();
+                if (lane == 0) s_cnt[w][a] = cnt;
             }
         }
-        if (lane == 0) {
-#pragma unroll
-            for (int a = 0; a < MAXA; ++a) {
-                const int i = ib + w + 4 * a;
-                if (i < i1) {
-                    // a row is never longer than its slot: an overrun is reported, not read
-                    if (FILL && cnt[a] > row_cap) atomicOr(status, ST_LIST_OVERFLOW);
-                    count[i] = FILL ? min(cnt[a], row_cap) : cnt[a];
-                }
+        __syncwarp();
+        if (lane < LC_MAXA) {
+            const int i = ib + w + LC_WARPS * lane;
+            if (i < i1) {
+                const int cnt = s_cnt[w][lane];
+                // a row is never longer than its slot: an overrun is reported, not read
+                if (FILL && cnt > row_cap) atomicOr(status, ST_LIST_OVERFLOW);
+                count[i] = FILL ? min(cnt, row_cap) : cnt;
             }
         }
     }
