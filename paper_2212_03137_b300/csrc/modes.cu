@@ -81,6 +81,29 @@ __device__ __forceinline__ double dot4(const double* __restrict__ a, int sa, con
     return (s0 + s1) + (s2 + s3);
 }
 
+// FP32 <-> FP64 conversions from the bit patterns, on the integer pipes: the integrator's
+// limit is its FP64 pipe (the B, A and O updates, 9 FP64 FMAs a mode), which these leave
+// alone.  Values equal the hardware conversion's: IEEE round-to-nearest-even for
+// double -> float, exact for float -> double.  Zeros, subnormal results, infinities and
+// NaNs are left to the hardware conversion.
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;                  // biased float exponent
+    if (e <= 0 || e >= 255) return (float)x;
+    unsigned r = ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;                         // the 29 dropped bits
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;   // a carry may reach the exponent
+    return __uint_as_float((hi & 0x80000000u) | r);
+}
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ bool finite_bits(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+
 // Exact free flow over dt/2 (Eq. (9) without forces): drift for the centroid, the
 // three-shear form of the rotation for n > 0 (determinant one whatever the rounding).
 __device__ __forceinline__ void free_half(int n, const double* c, double& q, double& pm) {
@@ -136,14 +159,14 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
                 const int dof = a * 3 + d;
                 const int ms = (int)(step % (unsigned long long)A.n_seg);
                 const size_t r = (size_t)ms * (size_t)(3 * A.N) + dof;
-                const double kick = c[MT_AMP] * (double)A.qtb_u[r];
+                const double kick = c[MT_AMP] * f32_to_f64(A.qtb_u[r]);
                 const double pnew = c[MT_C1] * pm + kick;
-                A.qtb_v[r] = (float)((pm + pnew) * c[MT_INV2M]);
-                A.qtb_F[r] = (float)(kick * A.inv_dt);
+                A.qtb_v[r] = f64_to_f32((pm + pnew) * c[MT_INV2M]);
+                A.qtb_F[r] = f64_to_f32(kick * A.inv_dt);
                 pm = pnew;
             } else {                                                  // O with white noise
                 const uint4 x = philox_draw(A.seed, (uint32_t)idx, step, TAG_OSTEP);
-                const double R = MIXED ? (double)normal_f32(x, 0) : normal_f64(x, 0);
+                const double R = MIXED ? f32_to_f64(normal_f32(x, 0)) : normal_f64(x, 0);
                 pm = c[MT_C1] * pm + c[MT_AMP] * R;
             }
             free_half(n, c, q, pm);                                   // A
@@ -152,26 +175,26 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
         }
     }
     qs[t] = q;
-    qf[t] = (float)q;
+    // mixed: the centroid slot carries the bead-independent FP64 centroid offset, rounded
+    // once; the other slots the FP32 modes for the fluctuation sum
+    if (MIXED) qf[t] = (n == 0) ? (valid ? f64_to_f32(q - A.anchor[a * 3 + d]) : 0.0f) : f64_to_f32(q);
     __syncthreads();
 
     float dv = 0.0f;
     if (valid) {
         const int base = la * 3 * P + d * P;
-        const int s = A.iperm[a];
-        const double anc = A.anchor[a * 3 + d];
         if (MIXED) {
             // FP64 centroid offset + FP32 fluctuation sum: the bead position only feeds the
             // FP32 pair kernel, where 1e-7 relative on sub-Angstrom fluctuations is far
             // below the pair arithmetic's own rounding.
             float acc = 0.0f;
             acc = dot4(Tsf + n, P, qf + base, 1, P);
-            xr[t] = (float)(qs[base] - anc) + acc;
+            xr[t] = qf[base] + acc;
         } else {
             double acc = 0.0;
             acc = dot4(Tsd + n, P, qs + base, 0, P);
-            A.pos_d[((size_t)d * A.N + s) * P + n] = acc;
-            xr[t] = (float)(acc - anc);
+            A.pos_d[((size_t)d * A.N + A.iperm[a]) * P + n] = acc;
+            xr[t] = f64_to_f32(acc - A.anchor[a * 3 + d]);
         }
     }
     __syncthreads();
@@ -245,28 +268,36 @@ __device__ __forceinline__ void project_body(const ProjectArgs& A, int bx, unsig
             if (MIXED) Tsf[k] = A.Tpf[k];
             else Tsd[k] = A.Tp[k];
         }
+    long long v = 0;
     if (valid) {
         if (MIXED) {
-            const long long v = A.Ffix[idx];
+            v = A.Ffix[idx];
             Fi[t] = v;
             Ff[t] = __ll2float_rn(v) * (1.0f / FIX_SCALE_F);   // one conversion per bead force
         } else {
             Fs[t] = A.Fd[idx];
         }
     }
+    // f_0 = mean bead force: exact integer sum of the fixed-point forces; with P <= 32 the
+    // P lanes of an (atom, dim) are an aligned group of one warp and add by shuffles
+    if (MIXED && P <= 32)
+        for (int off = 1; off < P; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     __syncthreads();
     if (valid) {
         const int base = la * 3 * P + d * P;
         double f;
         if (MIXED) {
-            if (n == 0) {   // f_0 = mean bead force: exact integer sum of the fixed-point forces
-                long long sum = 0;
-                for (int b = 0; b < P; ++b) sum += Fi[base + b];
+            if (n == 0) {
+                long long sum = v;
+                if (P > 32) {
+                    sum = 0;
+                    for (int b = 0; b < P; ++b) sum += Fi[base + b];
+                }
                 f = (double)sum * (1.0 / (FIX_SCALE * (double)P));   // power of two: exact scaling
             } else {
                 float acc = 0.0f;
                 acc = dot4(Tsf + n, P, Ff + base, 0, P);
-                f = (double)acc;
+                f = f32_to_f64(acc);
             }
         } else {
             double acc = 0.0;
@@ -277,7 +308,7 @@ __device__ __forceinline__ void project_body(const ProjectArgs& A, int bx, unsig
         if (KICK) {
             const double p = A.Pm[idx] + A.half_dt_acc * f;
             A.Pm[idx] = p;
-            if (!isfinite(p)) atomicOr(A.status, ST_NONFINITE);
+            if (!finite_bits(p)) atomicOr(A.status, ST_NONFINITE);
         }
     }
     if (KICK && bx == 0 && t == 0) *A.step_ctr += 1ull;
