@@ -177,6 +177,26 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, float* red_
     const int chunk = ((kb - ka + W - 1) / W + JPW - 1) / JPW * JPW;
     const int kw0 = min(kb, ka + wa * chunk), k1 = min(kb, kw0 + chunk);
     int k = kw0 + jsub;
+    if (P == 2 || P == 4) {
+        // few beads: little arithmetic per entry, so the loop waits on the list stream and the
+        // dependent position gathers; four entries per lane in flight.  (With P = 1 the extra
+        // registers cost more occupancy than the deeper pipeline gains: measured slower.)
+        for (; k + 3 * JPW < k1; k += 4 * JPW) {
+            int4 e[4];
+            float4 q[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) e[v] = __ldg(&nbr[k + v * JPW]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) q[v] = __ldg(&pl[entry_j(e[v].x) * P]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const bool h = entry_is_h(e[v].x);
+                pair_term<ALL, ENERGY>(__int_as_float(e[v].y) + (q[v].x - xi[0]), __int_as_float(e[v].z) + (q[v].y - yi[0]),
+                                       __int_as_float(e[v].w) + (q[v].z - zi[0]), h ? qH : qO, Oi && !h, c, fx[0], fy[0],
+                                       fz[0], en[0]);
+            }
+        }
+    }
     // two list entries per iteration: both entries and all their loads are in flight together
     for (; k + JPW < k1; k += 2 * JPW) {
         const int4 e0 = __ldg(&nbr[k]);

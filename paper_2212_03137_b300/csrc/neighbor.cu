@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(LC_THREADS, 4) k_list_cells(
     const double* anchor, int* count, const int* start, int4* nbr, int row_cap, unsigned* status) {
     if (!*flag) return;
     __shared__ int c_beg[125], c_cnt[125], c_off[126];
-    __shared__ float c_sx[125], c_sy[125], c_sz[125];
+    __shared__ float4 c_sh[125], c_lo[125];   // periodic shift of each stencil cell (hi, lo parts)
     __shared__ float4 s_w[LC_CHUNK];     // shifted wrapped centroid (prefilter), .w = mol as int bits
     __shared__ float4 s_l[LC_CHUNK];     // low parts, .w = j | H bit as int bits
     __shared__ float4 s_s[LC_CHUNK];     // unshifted wrapped centroid (hi), .w = stencil cell as int bits
@@ -265,9 +265,9 @@ __global__ void __launch_bounds__(LC_THREADS, 4) k_list_cells(
         const int cj = (z * n_c + y) * n_c + x;
         c_beg[t] = cell_start[cj];
         c_cnt[t] = cell_start[cj + 1] - c_beg[t];
-        c_sx[t] = sx;
-        c_sy[t] = sy;
-        c_sz[t] = sz;
+        c_sh[t] = make_float4(sx, sy, sz, 0.f);
+        c_lo[t] = make_float4(sx > 0.f ? Llo : (sx < 0.f ? -Llo : 0.f), sy > 0.f ? Llo : (sy < 0.f ? -Llo : 0.f),
+                              sz > 0.f ? Llo : (sz < 0.f ? -Llo : 0.f), 0.f);
     }
     __syncthreads();
     if (t == 0) {
@@ -286,8 +286,13 @@ __global__ void __launch_bounds__(LC_THREADS, 4) k_list_cells(
         if (lane < LC_MAXA) s_cnt[w][lane] = 0;
         for (int m0 = 0; m0 < M; m0 += LC_CHUNK) {
             const int mc = min(LC_CHUNK, M - m0);
+            const int mpad = (mc + 31) & ~31;   // slots mc .. mpad-1 hold candidates that never pass
             __syncthreads();
-            for (int e = t; e < mc; e += LC_THREADS) {
+            for (int e = t; e < mpad; e += LC_THREADS) {
+                if (e >= mc) {
+                    s_w[e] = make_float4(INFINITY, 0.f, 0.f, __int_as_float(-1));
+                    continue;
+                }
                 const int m = m0 + e;
                 int lo = 0, hi = 124;   // stencil cell of candidate m (binary search over 125 offsets)
                 while (lo < hi) {
@@ -299,7 +304,8 @@ __global__ void __launch_bounds__(LC_THREADS, 4) k_list_cells(
                 const int j = c_beg[k] + (m - c_off[k]);
                 const float4 wj = cw[j];
                 const float4 lj = cwl[j];
-                s_w[e] = make_float4(wj.x + c_sx[k], wj.y + c_sy[k], wj.z + c_sz[k], __int_as_float(mol_s[j]));
+                const float4 sh = c_sh[k];
+                s_w[e] = make_float4(wj.x + sh.x, wj.y + sh.y, wj.z + sh.z, __int_as_float(mol_s[j]));
                 s_l[e] = make_float4(lj.x, lj.y, lj.z, __int_as_float(j | (type_s[j] ? (int)0x80000000u : 0)));
                 s_s[e] = make_float4(wj.x, wj.y, wj.z, __int_as_float(k));
             }
@@ -329,10 +335,10 @@ __global__ void __launch_bounds__(LC_THREADS, 4) k_list_cells(
                             const float4 sl = s_l[e];
                             const float4 wj = s_s[e];
                             const int k = __float_as_int(wj.w);
-                            const float kx = c_sx[k], ky = c_sy[k], kz = c_sz[k];
-                            const float Dx = sep_df(wj.x, sl.x, wi.x, li.x, kx, kx > 0.f ? Llo : (kx < 0.f ? -Llo : 0.f));
-                            const float Dy = sep_df(wj.y, sl.y, wi.y, li.y, ky, ky > 0.f ? Llo : (ky < 0.f ? -Llo : 0.f));
-                            const float Dz = sep_df(wj.z, sl.z, wi.z, li.z, kz, kz > 0.f ? Llo : (kz < 0.f ? -Llo : 0.f));
+                            const float4 sh = c_sh[k], lo = c_lo[k];
+                            const float Dx = sep_df(wj.x, sl.x, wi.x, li.x, sh.x, lo.x);
+                            const float Dy = sep_df(wj.y, sl.y, wi.y, li.y, sh.y, lo.y);
+                            const float Dz = sep_df(wj.z, sl.z, wi.z, li.z, sh.z, lo.z);
                             nbr[pos] = make_int4(__float_as_int(sl.w), __float_as_int(Dx), __float_as_int(Dy),
                                                  __float_as_int(Dz));
                         }
@@ -340,40 +346,35 @@ __global__ void __launch_bounds__(LC_THREADS, 4) k_list_cells(
                     base += n;
                     __syncwarp();
                 };
-                for (int eb = 0; eb < mc; eb += 32) {
+                for (int eb = 0; eb < mpad; eb += 32) {
                     const int e = eb + lane;
-                    bool acc = false;
-                    if (e < mc) {
-                        const float4 sw = s_w[e];
-                        if (__float_as_int(sw.w) != mi) {
-                            const float ddx = sw.x - wi.x, ddy = sw.y - wi.y, ddz = sw.z - wi.z;
-                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            if (r2 < lo2) {
-                                acc = true;
-                            } else if (r2 <= hi2) {   // borderline: the exact FP64 definition decides
-                                const int j = __float_as_int(s_l[e].w) & 0x7fffffff;
-                                const int aj = perm[j];
-                                const double ex = min_image_rn(__dsub_rn(anchor[aj * 3], anchor[ai * 3]), L);
-                                const double ey = min_image_rn(__dsub_rn(anchor[aj * 3 + 1], anchor[ai * 3 + 1]), L);
-                                const double ez = min_image_rn(__dsub_rn(anchor[aj * 3 + 2], anchor[ai * 3 + 2]), L);
-                                const double d2 =
-                                    __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-                                acc = d2 < r2max;
-                            }
-                        }
+                    const float4 sw = s_w[e];
+                    const float ddx = sw.x - wi.x, ddy = sw.y - wi.y, ddz = sw.z - wi.z;
+                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    const bool other = __float_as_int(sw.w) != mi;
+                    bool acc = other && r2 < lo2;
+                    const bool band = other && r2 >= lo2 && r2 <= hi2;
+                    if (__any_sync(0xffffffffu, band) && band) {   // borderline: the exact FP64 definition decides
+                        const int j = __float_as_int(s_l[e].w) & 0x7fffffff;
+                        const int aj = perm[j];
+                        const double ex = min_image_rn(__dsub_rn(anchor[aj * 3], anchor[ai * 3]), L);
+                        const double ey = min_image_rn(__dsub_rn(anchor[aj * 3 + 1], anchor[ai * 3 + 1]), L);
+                        const double ez = min_image_rn(__dsub_rn(anchor[aj * 3 + 2], anchor[ai * 3 + 2]), L);
+                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                        acc = d2 < r2max;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, acc);
                     const int nacc = __popc(bal);
                     if (FILL) {
-                        if (qn + nacc > 32) {   // make room: write the queue first
-                            flush(qn);
-                            qn = 0;
-                        }
-                        if (acc) s_q[w][qn + __popc(bal & lt_mask)] = e;
-                        qn += nacc;
-                        if (qn == 32) {
+                        // queue slots qn, qn+1, ... in candidate order; a full queue is written at once
+                        const int slot = qn + __popc(bal & lt_mask);
+                        if (acc && slot < 32) s_q[w][slot] = e;
+                        if (qn + nacc >= 32) {
                             flush(32);
-                            qn = 0;
+                            if (acc && slot >= 32) s_q[w][slot - 32] = e;
+                            qn += nacc - 32;
+                        } else {
+                            qn += nacc;
                         }
                     }
                     cnt += nacc;
