@@ -29,11 +29,12 @@ struct qhp_batch_s {
     std::vector<cudaStream_t> sys_streams;   // the members' streams before they joined
     cudaStream_t own_stream = nullptr, stream = nullptr, aux = nullptr;
     qhp::BatchStage integrate, bonded, project;
-    qhp::BatchStage pair[7];                // one per bead count (index log2 P)
+    qhp::BatchStage pair[qhp::BATCH_PAIR_STAGES];   // one per (bead count, small-box path, warps per atom)
     qhp::CheckArgs* check_args = nullptr;   // device [n_sys]
     cudaGraphExec_t exec = nullptr;
     std::vector<int4*> nbr_seen;            // list buffers the stages were built for
     std::vector<int> rowcap_seen;
+    std::vector<int> pairw_seen;            // and the warps-per-atom settings
     int64_t steps = 0;
     int64_t launches = 0;
     int kernels_per_step = 0;
@@ -104,9 +105,11 @@ int build_stages(qhp_batch_s* b) {
     TRY(batch_stage_project(v, b->project));
     b->nbr_seen.clear();
     b->rowcap_seen.clear();
+    b->pairw_seen.clear();
     for (qhp_system_s* s : v) {
         b->nbr_seen.push_back(s->nbr);
         b->rowcap_seen.push_back(s->row_cap);
+        b->pairw_seen.push_back(s->pair_w);
     }
     drop_graph(b);
     return QHP_OK;
@@ -201,7 +204,7 @@ int capture(qhp_batch_s* b) {
     mark(4);
     fail(launch_batch_project(b->project, b->stream), "batch project");
     mark(5);
-    for (int k = 0; k < 7; ++k) kernels += b->pair[k].n_items > 0 ? 1 : 0;
+    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) kernels += b->pair[k].n_items > 0 ? 1 : 0;
     kernels += 2;
     cudaGraph_t g2 = nullptr;
     e = cudaStreamEndCapture(b->stream, &g2);
@@ -220,7 +223,9 @@ int capture(qhp_batch_s* b) {
 
 bool stale(qhp_batch_s* b) {
     for (size_t k = 0; k < b->sys.size(); ++k)
-        if (b->sys[k]->nbr != b->nbr_seen[k] || b->sys[k]->row_cap != b->rowcap_seen[k]) return true;
+        if (b->sys[k]->nbr != b->nbr_seen[k] || b->sys[k]->row_cap != b->rowcap_seen[k] ||
+            b->sys[k]->pair_w != b->pairw_seen[k])
+            return true;
     return false;
 }
 
@@ -353,7 +358,7 @@ int qhp_destroy_batch(qhp_batch b) {
     }
     drop_graph(b);
     stage_free(b->integrate);
-    for (int k = 0; k < 7; ++k) stage_free(b->pair[k]);
+    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) stage_free(b->pair[k]);
     stage_free(b->bonded);
     stage_free(b->project);
     cudaFree(b->check_args);
@@ -461,10 +466,10 @@ int qhp_batch_get_info(qhp_batch b, qhp_batch_info* out) {
     out->steps = b->steps;
     out->kernels_per_step = b->kernels_per_step;
     out->grid_integrate = b->integrate.grid;
-    for (int k = 0; k < 7; ++k) out->grid_pair += b->pair[k].grid;
+    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) out->grid_pair += b->pair[k].grid;
     out->grid_bonded = b->bonded.grid;
     out->grid_project = b->project.grid;
-    for (int k = 0; k < 7; ++k) out->items_pair += b->pair[k].n_items;
+    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) out->items_pair += b->pair[k].n_items;
     // kernels run inside the conditional rebuild bodies, counted on the device
     cudaStreamSynchronize(b->stream);
     int64_t extra = 0;

@@ -276,8 +276,6 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, float* red_
 // keeps 12 blocks.
 template <int P>
 __host__ __device__ constexpr int pair_min_blocks() { return (P == 16 || P == 32) ? 16 : 0; }
-template <int P>
-__host__ __device__ constexpr int pair_batch_min_blocks() { return (P == 16 || P == 32) ? 12 : 0; }
 
 template <int P, int W, bool ALL, bool ENERGY>
 __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_min_blocks<P>()) k_pair_mixed(const __grid_constant__ PairArgs A) {
@@ -285,28 +283,24 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_min_blocks<P>()) k_pair_
     pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, red);
 }
 
-// Batched systems: one persistent launch per bead count, over the (system, block) items of
-// the systems with that P; each item's warps per atom and list mode select the
-// specialisation (uniform over the block).  One launch per P keeps every launch at the
-// registers of its own bead count.
+// Batched systems: one persistent launch per (bead count, small-box path, warps per atom)
+// present, over the (system, block) items of the systems of that kind.  Each launch carries
+// one specialisation, so it runs at that specialisation's registers and residency (the same
+// as the single-system kernel).
+// The persistent item loop keeps a few more values live than the single-system kernel:
+// 12 resident blocks (40 registers) for P = 16 and 32 instead of 16.
 template <int P>
+__host__ __device__ constexpr int pair_batch_min_blocks() { return (P == 16 || P == 32) ? 12 : 0; }
+
+template <int P, int W, bool ALL>
 __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_batch_min_blocks<P>()) k_pair_batch(const PairArgs* __restrict__ args,
-                                                                const int2* __restrict__ items,
-                                                                const int* __restrict__ ranges) {
+                                                                                      const int2* __restrict__ items,
+                                                                                      const int* __restrict__ ranges) {
     __shared__ float red[PAIR_RED];
     for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
         const int2 w = items[it];
-        const PairArgs& A = args[w.x];
         __syncthreads();   // the previous item's reduction has been read
-        if (A.all) {
-            if (A.W == 4) pair_body<P, 4, true, false>(A, w.y, red);
-            else if (A.W == 2) pair_body<P, 2, true, false>(A, w.y, red);
-            else pair_body<P, 1, true, false>(A, w.y, red);
-        } else {
-            if (A.W == 4) pair_body<P, 4, false, false>(A, w.y, red);
-            else if (A.W == 2) pair_body<P, 2, false, false>(A, w.y, red);
-            else pair_body<P, 1, false, false>(A, w.y, red);
-        }
+        pair_body<P, W, ALL, false>(args[w.x], w.y, red);
     }
 }
 
@@ -691,54 +685,82 @@ cudaError_t launch_bonded(qhp_system_s* s, bool energy) {
 
 // Batched stages (mixed precision).  Pair items are blocks of PAIR_WARPS / W atoms, costed
 // by the bead-pair work of their list rows (row length x max(P, 32) lanes); one stage per
-// bead count (stage index log2 P).
-template <int P>
-const void* pair_batch_kernel() { return (const void*)k_pair_batch<P>; }
+// (log2 P, small-box path, W), index batch_pair_stage(lp, all, W).
+int batch_pair_stage(int lp, int all, int W) { return (lp * 2 + all) * 3 + (W == 4 ? 2 : W == 2 ? 1 : 0); }
 
-const void* pair_batch_kernel_for(int P) {
-    switch (P) {
-        case 1: return pair_batch_kernel<1>();
-        case 2: return pair_batch_kernel<2>();
-        case 4: return pair_batch_kernel<4>();
-        case 8: return pair_batch_kernel<8>();
-        case 16: return pair_batch_kernel<16>();
-        case 32: return pair_batch_kernel<32>();
-        default: return pair_batch_kernel<64>();
+template <int P>
+struct PairBatchVariants {
+    template <int W, bool ALL>
+    static void go(const BatchStage* s, cudaStream_t st, const void** ptr) {
+        if (ptr) *ptr = (const void*)k_pair_batch<P, W, ALL>;
+        else k_pair_batch<P, W, ALL><<<s->grid, 32 * PAIR_WARPS, 0, st>>>((const PairArgs*)s->args, s->items, s->ranges);
+    }
+    // launch stage s (ptr == nullptr) or return its kernel (ptr != nullptr)
+    static void dispatch(int all, int W, const BatchStage* s, cudaStream_t st, const void** ptr) {
+        if (all) {
+            if (W == 4) go<4, true>(s, st, ptr);
+            else if (W == 2) go<2, true>(s, st, ptr);
+            else go<1, true>(s, st, ptr);
+        } else {
+            if (W == 4) go<4, false>(s, st, ptr);
+            else if (W == 2) go<2, false>(s, st, ptr);
+            else go<1, false>(s, st, ptr);
+        }
+    }
+};
+
+void pair_batch_dispatch(int lp, int all, int W, const BatchStage* s, cudaStream_t st, const void** ptr) {
+    switch (lp) {
+        case 0: PairBatchVariants<1>::dispatch(all, W, s, st, ptr); break;
+        case 1: PairBatchVariants<2>::dispatch(all, W, s, st, ptr); break;
+        case 2: PairBatchVariants<4>::dispatch(all, W, s, st, ptr); break;
+        case 3: PairBatchVariants<8>::dispatch(all, W, s, st, ptr); break;
+        case 4: PairBatchVariants<16>::dispatch(all, W, s, st, ptr); break;
+        case 5: PairBatchVariants<32>::dispatch(all, W, s, st, ptr); break;
+        default: PairBatchVariants<64>::dispatch(all, W, s, st, ptr); break;
     }
 }
 
-int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[7]*/) {
-    for (int lp = 0; lp < 7; ++lp) {
-        const int P = 1 << lp;
-        std::vector<PairArgs> a;
-        std::vector<int2> items;
-        std::vector<double> cost;
-        for (size_t k = 0; k < v.size(); ++k) {
-            const qhp_system_s* s = v[k];
-            if (s->P != P) continue;
-            const int idx = (int)a.size();
-            a.push_back(make_pair_args(s));
-            const int apb = PAIR_WARPS / a.back().W;
-            const int nb = (s->N + apb - 1) / apb;
-            std::vector<int> cnt(s->N);
-            QHP_CUDA(cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * s->N, cudaMemcpyDeviceToHost));
-            const double lanes = (double)std::max(P, 32) / 32.0;
-            for (int b = 0; b < nb; ++b) {
-                double c = 0.0;
-                for (int i = b * apb; i < std::min(s->N, (b + 1) * apb); ++i) c += (double)cnt[i] * lanes;
-                items.push_back(make_int2(idx, b));
-                cost.push_back(c + 8.0);
+int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[BATCH_PAIR_STAGES]*/) {
+    const int Ws[3] = {1, 2, 4};
+    for (int lp = 0; lp < 7; ++lp)
+        for (int all = 0; all < 2; ++all)
+            for (int W : Ws) {
+                const int P = 1 << lp;
+                BatchStage& S = st[batch_pair_stage(lp, all, W)];
+                std::vector<PairArgs> a;
+                std::vector<int2> items;
+                std::vector<double> cost;
+                for (size_t k = 0; k < v.size(); ++k) {
+                    const qhp_system_s* s = v[k];
+                    if (s->P != P) continue;
+                    const PairArgs A = make_pair_args(s);
+                    if (A.all != all || A.W != W) continue;
+                    const int idx = (int)a.size();
+                    a.push_back(A);
+                    const int apb = PAIR_WARPS / W;
+                    const int nb = (s->N + apb - 1) / apb;
+                    std::vector<int> cnt(s->N);
+                    QHP_CUDA(cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * s->N, cudaMemcpyDeviceToHost));
+                    const double lanes = (double)std::max(P, 32) / 32.0;
+                    for (int b = 0; b < nb; ++b) {
+                        double c = 0.0;
+                        for (int i = b * apb; i < std::min(s->N, (b + 1) * apb); ++i) c += (double)cnt[i] * lanes;
+                        items.push_back(make_int2(idx, b));
+                        cost.push_back(c + 8.0);
+                    }
+                }
+                if (a.empty()) {
+                    stage_free(S);
+                    continue;
+                }
+                const void* fn = nullptr;
+                pair_batch_dispatch(lp, all, W, nullptr, nullptr, &fn);
+                int per_sm = 0;
+                QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * PAIR_WARPS, 0));
+                S.smem = 0;
+                TRY(stage_upload(S, a.data(), sizeof(PairArgs) * a.size(), items, cost, std::max(1, per_sm) * sm_count()));
             }
-        }
-        if (a.empty()) {
-            stage_free(st[lp]);
-            continue;
-        }
-        int per_sm = 0;
-        QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_batch_kernel_for(P), 32 * PAIR_WARPS, 0));
-        st[lp].smem = 0;
-        TRY(stage_upload(st[lp], a.data(), sizeof(PairArgs) * a.size(), items, cost, std::max(1, per_sm) * sm_count()));
-    }
     return QHP_OK;
 }
 
@@ -761,21 +783,16 @@ int batch_stage_bonded(const std::vector<qhp_system_s*>& v, BatchStage& st) {
 }
 
 cudaError_t launch_batch_pair(const BatchStage* st, cudaStream_t stream) {
-    for (int lp = 0; lp < 7; ++lp) {
-        if (st[lp].n_items == 0) continue;
-        const PairArgs* a = (const PairArgs*)st[lp].args;
-        switch (lp) {
-            case 0: k_pair_batch<1><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
-            case 1: k_pair_batch<2><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
-            case 2: k_pair_batch<4><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
-            case 3: k_pair_batch<8><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
-            case 4: k_pair_batch<16><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
-            case 5: k_pair_batch<32><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
-            default: k_pair_batch<64><<<st[lp].grid, 32 * PAIR_WARPS, 0, stream>>>(a, st[lp].items, st[lp].ranges); break;
-        }
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    const int Ws[3] = {1, 2, 4};
+    for (int lp = 0; lp < 7; ++lp)
+        for (int all = 0; all < 2; ++all)
+            for (int W : Ws) {
+                const BatchStage& S = st[batch_pair_stage(lp, all, W)];
+                if (S.n_items == 0) continue;
+                pair_batch_dispatch(lp, all, W, &S, stream, nullptr);
+                const cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 

@@ -339,11 +339,12 @@ void stage_free(BatchStage& st);
 int sm_count();
 int batch_stage_integrate(const std::vector<qhp_system_s*>& v, BatchStage& st);
 int batch_stage_project(const std::vector<qhp_system_s*>& v, BatchStage& st);
-int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[7], by log2 P*/);
+constexpr int BATCH_PAIR_STAGES = 7 * 2 * 3;   // (log2 P, small-box path, W = 1, 2, 4)
+int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[BATCH_PAIR_STAGES]*/);
 int batch_stage_bonded(const std::vector<qhp_system_s*>& v, BatchStage& st);
 cudaError_t launch_batch_integrate(const BatchStage& st, cudaStream_t stream);
 cudaError_t launch_batch_project(const BatchStage& st, cudaStream_t stream);
-cudaError_t launch_batch_pair(const BatchStage* st /*[7]*/, cudaStream_t stream);   // one launch per P
+cudaError_t launch_batch_pair(const BatchStage* st /*[BATCH_PAIR_STAGES]*/, cudaStream_t stream);   // one launch per non-empty stage
 cudaError_t launch_batch_bonded(const BatchStage& st, cudaStream_t stream);
 // Per-system record of the batched list check (the single-system k_check, one thread each).
 struct CheckArgs {

@@ -43,7 +43,9 @@ def test_batch_equals_single_systems_bitwise():
         b.step(15)
         b.sync()
         info = qhp.qhp_batch_get_info(b.h)
-        assert info.n_sys == len(MIX) and info.steps == 25 and info.kernels_per_step == 4 + len({c.P for c in MIX})
+        # one pair launch per (bead count, small-box path, warps per atom) present
+        kinds = {(c.P, qhp.qhp_get_info(m.h).list_mode, 4 if c.P >= 16 else 1) for c, m in zip(MIX, members)}
+        assert info.n_sys == len(MIX) and info.steps == 25 and info.kernels_per_step == 4 + len(kinds)
         assert info.atom_beads == sum(3 * c.n_mol * c.P for c in MIX)
         for s, m in zip(singles, members):
             Qa, Pa = qhp.qhp_get_modes(s.h)
