@@ -197,6 +197,65 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, float* red_
             }
         }
     }
+    if (P >= 32) {
+        // all lanes walk the same entry: the warp's entries are staged in shared memory 32 at
+        // a time by asynchronous copies issued one block ahead, so that only the dependent
+        // position gather is left on the loop's critical path.  Same entry order and pairing
+        // as the loop below, hence the same sums.
+        __shared__ int4 s_e[PAIR_WARPS][2][32];
+        int4(*ring)[32] = s_e[w];
+        const auto stage = [&](int kb0, int slot) {
+            const int kk = kb0 + lane;
+            const bool in = kk < k1;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&ring[slot][lane]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(nbr + (in ? kk : kb0)),
+                         "r"(in ? 16 : 0)
+                         : "memory");
+        };
+        int slot = 0;
+        if (k < k1) stage(k, 0);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        for (int kb0 = k; kb0 < k1; kb0 += 32, slot ^= 1) {
+            if (kb0 + 32 < k1) stage(kb0 + 32, slot ^ 1);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this block's copies are done
+            __syncwarp();
+            const int n = min(32, k1 - kb0);
+            int q = 0;
+            for (; q + 1 < n; q += 2) {
+                const int4 e0 = ring[slot][q];
+                const int4 e1 = ring[slot][q + 1];
+                const int j0 = entry_j(e0.x) * P, j1 = entry_j(e1.x) * P;
+                const bool h0 = entry_is_h(e0.x), h1 = entry_is_h(e1.x);
+#pragma unroll
+                for (int u = 0; u < BPL; ++u) {
+                    const float4 a = __ldg(&pl[j0 + 32 * u]);
+                    const float4 b = __ldg(&pl[j1 + 32 * u]);
+                    pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
+                                           __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u],
+                                           fy[u], fz[u], en[u]);
+                    pair_term<ALL, ENERGY>(__int_as_float(e1.y) + (b.x - xi[u]), __int_as_float(e1.z) + (b.y - yi[u]),
+                                           __int_as_float(e1.w) + (b.z - zi[u]), h1 ? qH : qO, Oi && !h1, c, fx[u],
+                                           fy[u], fz[u], en[u]);
+                }
+            }
+            if (q < n) {
+                const int4 e0 = ring[slot][q];
+                const int j0 = entry_j(e0.x) * P;
+                const bool h0 = entry_is_h(e0.x);
+#pragma unroll
+                for (int u = 0; u < BPL; ++u) {
+                    const float4 a = __ldg(&pl[j0 + 32 * u]);
+                    pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
+                                           __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u],
+                                           fy[u], fz[u], en[u]);
+                }
+            }
+            __syncwarp();   // every lane is done with this slot before it is refilled
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        k = k1;
+    }
     // two list entries per iteration: both entries and all their loads are in flight together
     for (; k + JPW < k1; k += 2 * JPW) {
         const int4 e0 = __ldg(&nbr[k]);
@@ -270,10 +329,10 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, float* red_
 }
 
 // Residency: with P = 16 or 32 (one atom per block, lanes = beads) the loop is latency bound
-// and 16 resident blocks (64 warps, 32 registers a thread) measured 12% faster than 10-12;
-// with few beads the compiler's default allocation (minimum 0) is faster, and P = 64 (two
-// beads a lane) would spill.  The batched kernel, which carries every variant of its P,
-// keeps 12 blocks.
+// and 16 resident blocks (64 warps, 32 registers a thread) measured 12% faster than 10-12
+// (with the staged entries of P = 32: 0.300 ms at 16 blocks, 0.318 ms at 12); with few
+// beads the compiler's default allocation (minimum 0) is faster, and P = 64 (two beads a
+// lane) would spill.
 template <int P>
 __host__ __device__ constexpr int pair_min_blocks() { return (P == 16 || P == 32) ? 16 : 0; }
 
