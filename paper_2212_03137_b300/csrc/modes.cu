@@ -6,6 +6,7 @@
 // APB = 64/P whole atoms, i.e. 3*P*APB = 192 threads, one per (atom, dim, mode),
 // so the P x P bead transform of an atom happens in shared memory.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -166,8 +167,12 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
                 pm = pnew;
             } else {                                                  // O with white noise
                 const uint4 x = philox_draw(A.seed, (uint32_t)idx, step, TAG_OSTEP);
-                const double R = MIXED ? f32_to_f64(normal_f32(x, 0)) : normal_f64(x, 0);
-                pm = c[MT_C1] * pm + c[MT_AMP] * R;
+                if (MIXED) {   // FP32 normal: the kick amp * R is formed in FP32 (1e-7 relative)
+                    const float ampf = reinterpret_cast<const float*>(c + MT_AMPF)[0];
+                    pm = c[MT_C1] * pm + f32_to_f64(ampf * normal_f32(x, 0));
+                } else {
+                    pm = c[MT_C1] * pm + c[MT_AMP] * normal_f64(x, 0);
+                }
             }
             free_half(n, c, q, pm);                                   // A
             A.Q[idx] = q;
@@ -531,6 +536,8 @@ void mode_constants(qhp_system_s* s) {
             c[MT_C1] = m.c1[n];
             c[MT_AMP] = m.amp[n] * sqrt(mass);
             c[MT_INV2M] = 0.5 / mass;
+            const float ampf = (float)c[MT_AMP];
+            memcpy(&c[MT_AMPF], &ampf, sizeof ampf);
         }
     }
 }

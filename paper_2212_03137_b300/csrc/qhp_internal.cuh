@@ -103,6 +103,7 @@ enum : int {
     MT_C1 = 2,      // exp(-gamma_n dt)
     MT_AMP = 3,     // sqrt((1 - c1^2) m kT) (PILE) or sqrt((1 - c1^2) m) (adQTB), A^2/ps^2 units
     MT_INV2M = 4,   // 1 / (2 m)
+    MT_AMPF = 5,    // MT_AMP rounded to FP32, stored in the slot's first four bytes
     MT_N = 8
 };
 
