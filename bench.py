@@ -228,7 +228,10 @@ def run_ours(args, ws, rank, local):
         clocks = clk.summary()
         smax = float(peaks.get("sm_max_mhz", 2032.0))
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_tflops = n_sm * 128 * 2 * smax * 1e6 / 1e12
+        fp64 = cfg.precision == "fp64"
+        # FP32: 128 FMA lanes per SM; FP64 runs at 1/64 of that rate on this part
+        lanes = 2 if fp64 else 128
+        peak_tflops = n_sm * lanes * 2 * smax * 1e6 / 1e12
         flops_launch = FLOPS_PAIR * pairs + FLOPS_LJ * oo_pairs
         mean_pair_ms = float(np.mean(pair_ms))
         achieved = flops_launch / (mean_pair_ms * 1e-3) / 1e12
@@ -236,7 +239,7 @@ def run_ours(args, ws, rank, local):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32/i64/f64 (mixed)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if fp64 else "f32/i64/f64 (mixed)", "data": "synthetic",
             "ns_per_day": ns_day,
             "config": {"workload": args.workload, "n_molecules": cfg.n_mol, "n_atoms": N, "beads": P,
                        "box_A": cfg.box, "rc_A": cfg.rc, "skin_A": cfg.skin, "dt_fs": cfg.dt_fs,
@@ -251,7 +254,8 @@ def run_ours(args, ws, rank, local):
                          "traffic": traffic, "pairs_per_launch": pairs, "oo_pairs_per_launch": oo_pairs,
                          "flops_per_launch": flops_launch, "mean_launch_ms": mean_pair_ms,
                          "share_of_step": mean_pair_ms / ms_per_step,
-                         "peak_source": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} clock)"},
+                         "peak_source": f"{'FP64' if fp64 else 'FP32'} FMA: {n_sm} SMs x {lanes} lanes x 2 x "
+                                        f"{smax:.0f} MHz ({src} clock)"},
             "clocks": clocks,
             "gpu_launches": int(launches),
             "stage_ms": dict(zip(["integrate_transform", "list_check_rebuild", "pair", "bonded", "project_kick"],
