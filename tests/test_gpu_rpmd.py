@@ -4,6 +4,8 @@ estimators and short trajectories (RPMD with the PILE thermostat).
 Tolerances: FP64 path 1e-12 RMS relative force error and 1e-10 A on 10-step
 centroids; mixed path 1e-5 RMS relative force error and 1e-6 A on 10-step centroids.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -68,6 +70,28 @@ def test_cells_and_centroid_list_bit_exact(cfg):
         got = qhp.qhp_get_list_pairs(s.h)
         assert len(got) == len(set(map(tuple, got.tolist())))
         assert set(map(tuple, got.tolist())) == list_pairs_oracle(C, box.molecule, box.box, r_list)
+
+
+def test_list_with_crowded_cells():
+    """A 10 A skin makes the cells 9.9 A wide (5 per edge), about 98 atoms each. The list fill
+    then takes a cell's atoms in more than one pass, and an atom's ~12,000 candidates span many
+    staged chunks."""
+    cfg = dataclasses.replace(C2, skin=10.0, P=1)
+    with _sys(cfg) as s:
+        qhp.qhp_step_rpmd(s.h, 5)
+        qhp.qhp_build_list(s.h)
+        info = qhp.qhp_get_info(s.h)
+        assert info.list_mode == 1 and info.n_cells_per_edge == 5
+        Q, _ = qhp.qhp_get_modes(s.h)
+        box = cfg.system()
+        cell, _ = qhp.qhp_get_cells(s.h)
+        assert np.bincount(cell).max() > 64
+        got = qhp.qhp_get_list_pairs(s.h).astype(np.int64)
+    ref = neighbor.verlet_pairs(Q[:, :, 0], box.molecule, box.box, cfg.rc + cfg.skin).astype(np.int64)
+    n = np.int64(3 * cfg.n_mol)
+    g = np.sort(got[:, 0] * n + got[:, 1])
+    assert np.all(np.diff(g) > 0)   # no duplicates
+    np.testing.assert_array_equal(g, np.sort(ref[:, 0] * n + ref[:, 1]))
 
 
 @pytest.mark.parametrize("cfg", [C1, CONFIGS["grad_216w"]], ids=["64w_L12.42", "216w_L18.6"])
