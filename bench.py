@@ -271,6 +271,8 @@ def run_ours(args, ws, rank, local):
     if args.fp64 and rank == 0:
         out["fp64_gpu_path"] = _fp64_path(args, cfg, dev)
         out["speedup_vs_fp64_gpu_path"] = value / ws / out["fp64_gpu_path"]["value"]
+    if rank == 0 and args.workload == "grad_216w":
+        out["gradient"] = _time_gradient(qhp, h, cfg, N, P)
     sysobj.close()
     if rank == 0 and args.cpu_baseline:
         cb, err = _cpu_baseline(cfg, args)
@@ -403,6 +405,25 @@ def run_batch(args, ws, rank, local):
                                "sample": f"FP64 oracle on 8 of the 256 boxes (indices {list(map(int, picks))}): "
                                          "forces of 2 beads each + one BAOAB update, numpy, 1 thread"}
     return out
+
+
+def _time_gradient(qhp, h, cfg, N, P, block=15, reps=3):
+    """Wall time of the differentiable segment: J = (1/K) sum_k V(Q_0,k) over K = cfg.steps
+    BAOAB steps with the noise held fixed, and dJ/dtheta by the checkpointed adjoint (forward
+    segment, replays from checkpoints every `block` steps, backward sweep).  The call is
+    synchronous, so host wall time brackets the device work."""
+    import time
+    K = int(cfg.steps)
+    qhp.qhp_segment_grad(h, K, block, 0)   # warm-up
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        J, g = qhp.qhp_segment_grad(h, K, block, 0)
+        ts.append(time.perf_counter() - t0)
+    t = float(np.median(ts))
+    return {"K": K, "checkpoint_block": block, "observable": "centroid potential energy V(Q_0)",
+            "parameters": ["eps", "sigma", "q_O", "k_b", "k_theta"], "s_per_gradient": t,
+            "atom_bead_steps_per_s": N * P * K / t, "J": J, "dJ_dtheta": [float(x) for x in g]}
 
 
 def _e2e(args, h, N, P, step, dev, ws, inner=1):
