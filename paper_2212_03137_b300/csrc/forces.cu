@@ -363,8 +363,84 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_batch_min_blocks<P>()) k
     }
 }
 
+// FP64 path, small boxes: one warp per (sorted atom i, bead b), its lanes over i's list row,
+// then a fixed shuffle tree.  Every bead is its own warp, so a few hundred atoms still fill the
+// GPU (at 4,096 waters the gathers of single words measured 1.6x slower than the bead lanes).
 template <bool ENERGY>
-__global__ void __launch_bounds__(128) k_pair_fp64(int N, int P, const double* __restrict__ pos,
+__global__ void __launch_bounds__(128) k_pair_fp64_rows(int N, int P, const double* __restrict__ pos,
+                                                   const int* __restrict__ start, const int* __restrict__ count,
+                                                   const int4* __restrict__ nbr,
+                                                   const float* __restrict__ charge_s, const int* __restrict__ type_s,
+                                                   const int* __restrict__ perm, const double q_O, const double q_H,
+                                                   double* __restrict__ F, double* __restrict__ epair, PairConsts c,
+                                                   const unsigned* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (w >= N * P) return;   // whole warps
+    const int i = w / P, b = w % P;
+    const bool ok = (*status & ST_LIST_OVERFLOW) == 0u;
+    const double qi = (type_s[i] == 0 ? q_O : q_H) * c.ke_d;
+    const bool Oi = type_s[i] == 0;
+    const int k0 = start[i], k1 = ok ? k0 + count[i] : k0;
+    const double xi = pos[((size_t)0 * N + i) * P + b];
+    const double yi = pos[((size_t)1 * N + i) * P + b];
+    const double zi = pos[((size_t)2 * N + i) * P + b];
+    double fx = 0.0, fy = 0.0, fz = 0.0, en = 0.0;
+    for (int k = k0 + lane; k < k1; k += 32) {
+        const int ex = __ldg(&nbr[k].x);
+        const int j = entry_j(ex);
+        const bool Oj = !entry_is_h(ex);
+        const double qq = qi * (Oj ? q_O : q_H);
+        double dx = pos[((size_t)0 * N + j) * P + b] - xi;
+        double dy = pos[((size_t)1 * N + j) * P + b] - yi;
+        double dz = pos[((size_t)2 * N + j) * P + b] - zi;
+        dx -= c.L_d * rint(dx * c.invL_d);
+        dy -= c.L_d * rint(dy * c.invL_d);
+        dz -= c.L_d * rint(dz * c.invL_d);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < c.rc2_d) {
+            const double r = sqrt(r2);
+            const double rinv = 1.0 / r;
+            const double ar = c.alpha_d * r;
+            const double erfc_ar = erfc(ar);
+            const double ex2 = exp(-ar * ar);
+            const double rinv2 = rinv * rinv;
+            double g = qq * (erfc_ar * rinv2 + c.c2a_d * ex2 * rinv - c.sc_d) * rinv;
+            double ep = 0.0;
+            if (ENERGY) ep = qq * (erfc_ar * rinv - c.ecut_d + c.sc_d * (r - c.rc_d));
+            if (Oi && Oj) {
+                const double s2 = c.sig2_d * rinv2;
+                const double s6 = s2 * s2 * s2;
+                g += c.eps24_d * (2.0 * s6 * s6 - s6) * rinv2;
+                if (ENERGY) ep += c.eps4_d * (s6 * s6 - s6) - c.ljshift_d;
+            }
+            fx -= g * dx;
+            fy -= g * dy;
+            fz -= g * dz;
+            if (ENERGY) en += 0.5 * ep;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, off);
+        fy += __shfl_xor_sync(0xffffffffu, fy, off);
+        fz += __shfl_xor_sync(0xffffffffu, fz, off);
+        if (ENERGY) en += __shfl_xor_sync(0xffffffffu, en, off);
+    }
+    if (lane == 0) {
+        const int a = perm[i];
+        F[((size_t)a * 3 + 0) * P + b] = fx;
+        F[((size_t)a * 3 + 1) * P + b] = fy;
+        F[((size_t)a * 3 + 2) * P + b] = fz;
+        if (ENERGY) epair[(size_t)i * P + b] = en;
+    }
+}
+
+// FP64 path, large boxes: one warp per sorted atom, lanes = (entry slot, bead) as in the
+// mixed kernel (P <= 32 by slots, P = 64 two beads a lane), so a partner's beads load as
+// consecutive words.
+template <bool ENERGY>
+__global__ void __launch_bounds__(128) k_pair_fp64_beads(int N, int P, const double* __restrict__ pos,
                                                    const int* __restrict__ start, const int* __restrict__ count,
                                                    const int4* __restrict__ nbr,
                                                    const float* __restrict__ charge_s, const int* __restrict__ type_s,
@@ -699,6 +775,11 @@ BondArgs make_bond_args(const qhp_system_s* s) {
 
 }  // namespace
 
+// FP64 pair mapping: bead lanes from this many atoms up (16 warps per SM of 148), row lanes
+// below.  Measured: 64 waters 0.186 -> 0.088 ms and 216 waters 1.72 -> 1.29 ms with row lanes;
+// 4,096 waters 32.8 ms with bead lanes against 52.6 ms with row lanes.
+constexpr int FP64_BEAD_LANES_MIN_ATOMS = 148 * 16;
+
 cudaError_t launch_pair(qhp_system_s* s, bool energy) {
     const PairConsts c = make_pair_consts(s);
     const int grid = (s->N * 32 + 127) / 128;
@@ -714,15 +795,25 @@ cudaError_t launch_pair(qhp_system_s* s, bool energy) {
             case 64: pair_mixed_dispatch<64>(A, energy, s->stream); break;
             default: return cudaErrorInvalidValue;
         }
-    } else {
+    } else if (s->N >= FP64_BEAD_LANES_MIN_ATOMS) {   // a warp per atom fills the GPU
         if (energy)
-            k_pair_fp64<true><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
-                                                           s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O, s->Fd,
-                                                           s->e_pair_d, c, s->status);
+            k_pair_fp64_beads<true><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr,
+                                                                 s->charge_s, s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O,
+                                                                 s->Fd, s->e_pair_d, c, s->status);
         else
-            k_pair_fp64<false><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr, s->charge_s,
-                                                            s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O, s->Fd,
-                                                            s->e_pair_d, c, s->status);
+            k_pair_fp64_beads<false><<<grid, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr,
+                                                                  s->charge_s, s->type_s, s->perm, s->ff.q_O, -0.5 * s->ff.q_O,
+                                                                  s->Fd, s->e_pair_d, c, s->status);
+    } else {   // a warp per (atom, bead)
+        const int grid_rows = (int)(((int64_t)s->N * s->P * 32 + 127) / 128);
+        if (energy)
+            k_pair_fp64_rows<true><<<grid_rows, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr,
+                                                                     s->charge_s, s->type_s, s->perm, s->ff.q_O,
+                                                                     -0.5 * s->ff.q_O, s->Fd, s->e_pair_d, c, s->status);
+        else
+            k_pair_fp64_rows<false><<<grid_rows, 128, 0, s->stream>>>(s->N, s->P, s->pos_d, s->nbr_start, s->nbr_count, s->nbr,
+                                                                      s->charge_s, s->type_s, s->perm, s->ff.q_O,
+                                                                      -0.5 * s->ff.q_O, s->Fd, s->e_pair_d, c, s->status);
     }
     s->launches += 1;
     return cudaGetLastError();

@@ -169,6 +169,20 @@ def test_forces_fp64_list_small_box():
     assert rms_rel(F, Fo) < 1e-12
 
 
+def test_forces_fp64_bead_lanes():
+    """1,000 waters (3,000 atoms): the FP64 pair kernel runs with bead lanes (a warp per atom);
+    the smaller boxes above run with row lanes (a warp per atom and bead)."""
+    cfg = small_mixed_config(1000, P=4)
+    with _sys(cfg, precision="fp64") as s:
+        assert qhp.qhp_get_info(s.h).list_mode == 1
+        qhp.qhp_step_rpmd(s.h, 2)
+        qhp.qhp_compute_forces(s.h)
+        xb = qhp.qhp_get_beads(s.h)
+        F = qhp.qhp_get_forces(s.h)
+    _, Fo = force_fn(cfg.system(), cfg.rc, cells=True)(xb[[0, 3]])
+    assert rms_rel(F[[0, 3]], Fo) < 1e-12
+
+
 def test_forces_mixed_full_size_sampled_beads():
     """4,096 waters, P = 32: two beads compared over every atom (oracle cell-list sum)."""
     cfg = C2
