@@ -83,7 +83,7 @@ __device__ __forceinline__ double dot4(const double* __restrict__ a, int sa, con
 }
 
 // FP32 <-> FP64 conversions from the bit patterns, on the integer pipes: the integrator's
-// limit is its FP64 pipe (the B, A and O updates, 9 FP64 FMAs a mode), which these leave
+// limit is its FP64 pipe (the B, A and O updates, 8 FP64 FMAs a mode), which these leave
 // alone.  Values equal the hardware conversion's: IEEE round-to-nearest-even for
 // double -> float, exact for float -> double.  Zeros, subnormal results, infinities and
 // NaNs are left to the hardware conversion.
