@@ -251,9 +251,11 @@ int qhp_bar(const double* dU_A, int n_A, const double* dU_B, int n_B, double bet
 /* Batched systems (the paper's bead parallelism extended to many independent systems;
  * no counterpart in the paper).  A batch steps n_sys initialised mixed-precision systems
  * with the PILE or NVE thermostat together: each step is one CUDA graph of batched
- * launches (integrate, list check, pair - one launch per bead count present -, bonded,
- * projection; persistent grids over (system, block) work items) plus one conditional
- * rebuild chain per system that runs only when that system's list check fires.  Results equal stepping every system alone
+ * launches (integrate, list check, pair - one launch per (bead count, small-box path,
+ * warps per atom) present -, bonded, projection; persistent grids over (system, block)
+ * work items) plus one conditional rebuild chain per system that runs only when that
+ * system's list check fires.  kernels_per_step counts the batched launches.  Results equal
+ * stepping every system alone
  * with the same warps-per-atom setting.  The systems stay owned by the caller and must
  * outlive the batch; while batched, their work runs on the batch's stream (member calls
  * such as qhp_get_modes stay valid and ordered), and qhp_set_stream must not be called
