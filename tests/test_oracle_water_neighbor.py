@@ -31,6 +31,30 @@ def test_dsf_reduces_to_coulomb_law():
     np.testing.assert_allclose(g * r, COULOMB * (-0.84 * 0.42) / r ** 2, rtol=1e-6)
 
 
+def test_dsf_with_self_term_gives_the_madelung_energy():
+    """Rock salt (+-1 charges, nearest-neighbour distance a): the DSF pair sum plus the DSF
+    self term approximates the Ewald sum, -M k_e/a per ion pair with the Madelung constant
+    M = 1.747565 (Fennell & Gezelter 2006).  Without the self term it misses by > 5 %."""
+    n, a = 6, 2.82
+    idx = np.stack(np.meshgrid(*(np.arange(2 * n),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    x = idx * a
+    q = np.where(idx.sum(1) % 2 == 0, 1.0, -1.0)
+    L = 2 * n * a
+    ff = water.ForceField(alpha=0.25, rc=12.0)
+    assert 2 * ff.rc < L
+    pairs = 0.0
+    for i in range(len(x) - 1):
+        d = water.min_image(x[i + 1:] - x[i], L)
+        r = np.sqrt((d * d).sum(1))
+        m = r < ff.rc
+        e, _ = water.coulomb_dsf(r[m], q[i] * q[i + 1:][m], ff)
+        pairs += e.sum()
+    madelung = -1.747565 * COULOMB / a
+    per_pair = (pairs + water.dsf_self_energy(q, ff)) / (len(x) / 2)
+    assert abs(per_pair / madelung - 1.0) < 2e-4, per_pair / madelung
+    assert abs(pairs / (len(x) / 2) / madelung - 1.0) > 0.05
+
+
 def test_lj_minimum_at_two_to_one_sixth_sigma():
     ff = water.ForceField(rc=1e6)
     r = np.array([2 ** (1 / 6) * ff.sigma])
