@@ -133,6 +133,22 @@ def test_ring_polymer_hamiltonian_is_conserved_to_second_order():
     assert 0.2 < e2 / e1 < 0.3, (e1, e2)
 
 
+def test_centroid_virial_estimator_harmonic_identity():
+    """For V = 1/2 k x^2 per dof, -(1/2P) sum_b (x_b - Q_0).F_b = (k/2) sum_{n>0} Q_n^2 exactly
+    (x_b - Q_0 = sqrt(P) sum_{n>0} T_bn Q_n and sum_b (x_b - Q_0).Q_0 = 0), so the
+    centroid-virial kinetic estimator of any mode state is 3N kT/2 + (k/2) sum_{n>0} Q_n^2."""
+    P, n, omega0 = 8, 5, 40.0
+    prm = rpmd.Params(P=P, temperature=300.0, dt=0.0005, gamma0=1.0, seed=2)
+    masses = np.linspace(1.0, 16.0, n)
+    rng = np.random.default_rng(4)
+    st = rpmd.init_state(rng.standard_normal((n, 3)), masses, prm)
+    st.Q[..., 1:] = 0.3 * rng.standard_normal(st.Q[..., 1:].shape)
+    rpmd.evaluate_forces(st, prm, rpmd.harmonic_forces(omega0, masses))
+    k = masses[:, None] * omega0 ** 2 / ACC
+    expect = 1.5 * n * prm.kT + 0.5 * float(np.sum(k * np.sum(st.Q[..., 1:] ** 2, axis=-1)))
+    assert abs(rpmd.centroid_virial_kinetic(st, prm) - expect) < 1e-12 * abs(expect)
+
+
 def test_single_bead_step_is_classical_baoab():
     """P = 1: one step equals textbook BAOAB (Leimkuhler-Matthews) with the same normals."""
     n = 20
