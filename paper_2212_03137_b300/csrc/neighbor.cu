@@ -52,7 +52,9 @@ __device__ __forceinline__ double min_image_fast(double d, double L, double invL
 __device__ __forceinline__ int cell_coord(double C, double L, int n_c, double* frac_out) {
     const double t = __ddiv_rn(C, L);
     double frac = __dsub_rn(t, floor(t));
-    if (frac == 1.0) frac = 0.0;
+    // 1.0 can come from rounding; a NaN or infinite coordinate (a blown-up state, which the
+    // status word reports) goes to cell 0, so that no index is ever formed from it
+    if (!(frac >= 0.0 && frac < 1.0)) frac = 0.0;
     *frac_out = frac;
     int c = (int)floor(__dmul_rn(frac, (double)n_c));
     return c < n_c - 1 ? c : n_c - 1;
