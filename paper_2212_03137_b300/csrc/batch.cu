@@ -388,6 +388,7 @@ int qhp_batch_step(qhp_batch b, int n) {
         return QHP_ERR_ARG;
     }
     if (n == 0) return QHP_OK;
+    TraceRange tr("qhp_batch_step");
     // report a fault of an earlier batched step found by a member's last synchronising call
     if (stale(b)) TRY(build_stages(b));
     if (!b->exec) TRY(capture(b));

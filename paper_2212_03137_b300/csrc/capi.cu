@@ -781,11 +781,13 @@ int qhp_set_thermostat(qhp_sys s, const qhp_thermo* th) {
 
 int qhp_step_rpmd(qhp_sys s, int n) {
     if (!s) return QHP_ERR_ARG;
+    TraceRange tr("qhp_step_rpmd");
     return run_steps(s, n, false);
 }
 
 int qhp_step_adqtb(qhp_sys s, int n) {
     if (!s) return QHP_ERR_ARG;
+    TraceRange tr("qhp_step_adqtb");
     return run_steps(s, n, true);
 }
 
@@ -794,6 +796,7 @@ int qhp_compute_forces(qhp_sys s) {
         set_error("system not initialised");
         return QHP_ERR_STATE;
     }
+    TraceRange tr("qhp_compute_forces");
     TRY(enqueue_forces(s, !s->list_valid, false));
     s->forces_valid = true;
     s->list_valid = true;

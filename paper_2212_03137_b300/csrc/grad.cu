@@ -558,6 +558,7 @@ using namespace qhp;
 extern "C" {
 
 int qhp_energy_grad_device(qhp_sys s, const double* x, double* energy, double* dE_dx, double* dE_dtheta) {
+    TraceRange tr("qhp_energy_grad_device");
     if (!s || !s->beads_set) {
         set_error("qhp_energy_grad: system not initialised");
         return QHP_ERR_STATE;
@@ -650,6 +651,7 @@ int qhp_state_energies(qhp_sys s, const double* theta_A, const double* theta_B, 
 }
 
 int qhp_segment_grad(qhp_sys s, int K, int block, int observable, double* J, double* dJ_dtheta) {
+    TraceRange tr("qhp_segment_grad");
     if (!s || !s->beads_set) {
         set_error("qhp_segment_grad: system not initialised");
         return QHP_ERR_STATE;

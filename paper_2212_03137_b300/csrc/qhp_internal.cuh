@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -10,6 +11,15 @@
 #include "../../include/qhp.h"
 
 namespace qhp {
+
+// Host-side trace range around an entry point (header-only NVTX: a no-op unless a profiler
+// is attached), so that timelines show each call and the launches it enqueues.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // ------------------------------------------------------------------ units
 // kcal/mol, Angstrom, amu, ps.  ACC converts (kcal/mol)/amu to A^2/ps^2.
