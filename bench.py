@@ -71,7 +71,10 @@ class ClockSampler:
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = index
+        # nvidia-smi numbers every GPU of the node: map the CUDA device ordinal through
+        # CUDA_VISIBLE_DEVICES (an index or a UUID) so that the samples are this rank's GPU's
+        vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+        self.index = vis[index] if index < len(vis) else str(index)
         self.rows = []
         self.proc = None
         self.thread = None
