@@ -104,11 +104,16 @@ typedef struct {
     int n_cells_per_edge, reserved;
 } qhp_info;
 
-/* Create a system of n_atoms atoms in a cubic periodic box of edge box_L (A).
- * type[i]: 0 = O, 1 = H.  Molecules are consecutive (O, H, H) triples with
- * molecule[i] = i / 3.  pos: [n_atoms][3] initial positions (A), used as the
- * centroids Q_0.  precision: QHP_FP64 or QHP_MIXED.  Allocates nothing on the
- * device until qhp_set_beads.  Returns QHP_ERR_ARG for other layouts. */
+/* Create a system of n_atoms atoms in a cubic periodic box of edge box_L (A): the
+ * N-atom system whose quantum partition function Eq. (1) of Sec. II.A approximates by
+ * P ring-polymer replicas.  type[i]: 0 = O, 1 = H.  Molecules are consecutive
+ * (O, H, H) triples with molecule[i] = i / 3.  pos: [n_atoms][3] initial positions
+ * (A), used as the centroids Q_0 (the n = 0 mode of Eq. (4)).  precision: QHP_FP64 or
+ * QHP_MIXED.  Allocates nothing on the device until qhp_set_beads.  Returns
+ * QHP_ERR_ARG for other layouts.
+ * qhp_destroy_system frees the system's device memory, stream and graphs (the handle is
+ * invalid afterwards; NULL is accepted).  Neither has a counterpart in the paper: they
+ * are the lifetime of the state the paper's equations act on. */
 int qhp_create_system(qhp_sys* out, int n_atoms, const int* type, const int* molecule,
                       const double* pos, double box_L, int precision);
 int qhp_destroy_system(qhp_sys sys);
@@ -152,10 +157,15 @@ int qhp_compute_forces(qhp_sys sys);
 /* Synchronise the stream and report device-side faults. */
 int qhp_sync(qhp_sys sys);
 
+/* Estimators at the current state (the qhp_energy fields above; Eqs. (3), (6), (7),
+ * (21)).  Synchronous; out is a host struct. */
 int qhp_get_energy(qhp_sys sys, qhp_energy* out);
-/* Bead forces -grad V(x_i) of the last force evaluation, out[P][n_atoms][3]. */
+/* Bead forces F_i = -grad V(x_i) of the last force evaluation (the per-bead gradient of
+ * U_P, Eq. (3), before the projection of Eqs. (10)-(11)), out[P][n_atoms][3] host,
+ * kcal/mol/A.  Synchronous. */
 int qhp_get_forces(qhp_sys sys, double* out);
-/* Centroids Q_0, out[n_atoms][3] (unwrapped). */
+/* Centroids Q_0 = the n = 0 normal mode (Eq. (4) with T_i0 = 1/sqrt(P), so Q_0 is the
+ * bead average), out[n_atoms][3] host, A (unwrapped).  Synchronous. */
 int qhp_get_centroid(qhp_sys sys, double* out);
 /* Bead positions x_i = sqrt(P) sum_n T_in Q_n in FP64 (Eq. (4)), out[P][n_atoms][3]. */
 int qhp_get_beads(qhp_sys sys, double* out);
@@ -168,9 +178,13 @@ int qhp_set_modes_device(qhp_sys sys, const double* Q, const double* Pm);
 int qhp_get_modes_device(qhp_sys sys, double* Q, double* Pm);
 int qhp_get_forces_device(qhp_sys sys, double* out);
 
-/* Checkpoint: opaque blob of the whole dynamical state (modes, forces, step,
- * adQTB gamma, noise segment and records).  qhp_get_state with buf == NULL
- * writes the required size to *size. */
+/* Checkpoint (no counterpart in the paper: a restart facility around the state its
+ * equations evolve): opaque blob of the whole dynamical state (modes, forces, step,
+ * adQTB gamma, noise segment and records).  qhp_get_state with buf == NULL writes the
+ * required size to *size; otherwise buf (host, caller-owned, *size bytes) receives the
+ * blob, QHP_ERR_ARG if *size is too small.  qhp_set_state restores a blob taken from a
+ * system of the same size, bead count, precision and noise-segment length
+ * (QHP_ERR_ARG otherwise); stepping on from it gives the same trajectory bit for bit. */
 int qhp_get_state(qhp_sys sys, void* buf, size_t* size);
 int qhp_set_state(qhp_sys sys, const void* buf, size_t size);
 
@@ -233,7 +247,8 @@ int qhp_energy_grad(qhp_sys sys, double* energy, double* dE_dx, double* dE_dthet
 int qhp_energy_grad_device(qhp_sys sys, const double* x, double* energy, double* dE_dx, double* dE_dtheta);
 int qhp_segment_grad(qhp_sys sys, int K, int block, int observable, double* J, double* dJ_dtheta);
 
-/* Free-energy differences by path-integral BAR (Sec. IV, Eqs. (27)-(28), appendix A).
+/* Free-energy differences by path-integral BAR (Sec. V, Perspective 2, Eqs. (27)-(28);
+ * the single-bead variant of Appendix A).
  * qhp_state_energies: at the current beads, out[4] = {U_P(A), U_P(B), V_A(x_0), V_B(x_0)}:
  * the bead-averaged potential (Eq. (3)) and the potential of bead 0 alone, for the two
  * parameter sets theta_A, theta_B = (eps, sigma, q_O, k_b, k_theta) (q_H = -q_O/2; the
@@ -322,7 +337,9 @@ int qhp_set_stream(qhp_sys sys, void* stream);
 int qhp_estimators_noalloc(int n_atoms, int P, double temperature, const double* Q, const double* Pm,
                            const double* F, const double* mass, double* out, void* stream);
 
-/* Message of the last failure on this thread ("" if none). */
+/* Message of the last failure on this thread ("" if none).  Thread-local rather than
+ * per system: failures of qhp_create_system or qhp_bar have no system to attach to.
+ * The pointer stays valid until the next failing call on the same thread. */
 const char* qhp_last_error(void);
 
 #ifdef __cplusplus

@@ -26,7 +26,7 @@ quantum effects", arXiv 2212.03137):
 * ``respa``         - BAOAB-RESPA multiple time stepping and ring-polymer
   contraction of the slow (nonbonded) forces (Sec. III.A.2, Eqs. (18)-(20));
 * ``bar``           - the path-integral Bennett acceptance ratio and its
-  single-bead variant (Sec. IV, Eqs. (27)-(28), appendix A);
+  single-bead variant (Sec. V, Perspective 2, Eqs. (27)-(28); Appendix A);
 * ``gradients``     - dU_P/dx and dU_P/dtheta (analytic) for the force-field
   parameters theta = (eps, sigma, q_O, k_b, k_theta), and the gradient of a
   K-step trajectory average by central differences of whole trajectories.

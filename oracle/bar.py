@@ -1,4 +1,4 @@
-"""Path-integral Bennett acceptance ratio (Sec. IV, Eqs. (27)-(28); appendix A), FP64.
+"""Path-integral Bennett acceptance ratio (Sec. V, Perspective 2, Eqs. (27)-(28); Appendix A), FP64.
 
 Two thermodynamic states A and B of the same system (here: two force-field parameter
 sets).  From configurations sampled in each state, dU = U_{B,P} - U_{A,P} with U_P the

@@ -1,4 +1,4 @@
-// Path-integral Bennett acceptance ratio (Sec. IV, Eqs. (27)-(28)): the self-consistent
+// Path-integral Bennett acceptance ratio (Sec. V, Perspective 2, Eqs. (27)-(28)): the self-consistent
 // solution for Dlt F_AB = F_B - F_A from dU = U_B - U_A sampled in state A and in state B.
 // The sums over samples run on the device (fixed-order block sums, FP64); the host iterates
 //     Dlt F = C + ln(<f(-dU + C)>_B / <f(dU - C)>_A) / beta,  C = Dlt F + ln(n_B / n_A) / beta

@@ -1,4 +1,4 @@
-"""PI-BAR (Sec. IV, Eqs. (27)-(28), appendix A) on the CUDA path against the oracle."""
+"""PI-BAR (Sec. V, Perspective 2, Eqs. (27)-(28); Appendix A) on the CUDA path against the oracle."""
 import math
 
 import numpy as np
