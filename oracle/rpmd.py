@@ -34,6 +34,7 @@ class Params:
     seed: int
     hbar: float = HBAR
     integrator: str = "baoab"   # "baoab" (exact A) or "bcocb" (Cayley A, Sec. III.A.1)
+    thermostat: str = "pile"    # "pile" (Eq. (16)) or "nve": no O step, the flow of Eq. (9) alone
 
     @property
     def kT(self) -> float:
@@ -142,7 +143,10 @@ def cayley_flow(q, p, m, w: float, h: float):
 
 
 def ou(state: State, prm: Params, masses: np.ndarray, dt: float, noise: np.ndarray | None = None) -> None:
-    """O: exact Ornstein-Uhlenbeck update with friction gamma_n (Eq. (16)) over dt."""
+    """O: exact Ornstein-Uhlenbeck update with friction gamma_n (Eq. (16)) over dt.  With the
+    "nve" thermostat there is no friction and no noise, so O is the identity."""
+    if prm.thermostat == "nve":
+        return
     N, P = state.Q.shape[0], prm.P
     c1 = np.exp(-prm.gammas() * dt)                               # [P]
     if noise is None:

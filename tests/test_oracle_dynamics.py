@@ -133,6 +133,61 @@ def test_ring_polymer_hamiltonian_is_conserved_to_second_order():
     assert 0.2 < e2 / e1 < 0.3, (e1, e2)
 
 
+def _langevin_momentum_acf(t, w, g):
+    """<p(t) p(0)> / (m kT) of a stationary Langevin oscillator dq = p/m dt,
+    dp = -m w^2 q dt - g p dt + sqrt(2 g m kT) dW (textbook result; w = 0 is the free particle)."""
+    if w == 0.0:
+        return np.exp(-g * t)
+    d = w * w - 0.25 * g * g
+    if abs(d) < 1e-12 * w * w:
+        return np.exp(-w * t) * (1.0 - w * t)
+    if d > 0:
+        w1 = math.sqrt(d)
+        return np.exp(-0.5 * g * t) * (np.cos(w1 * t) - 0.5 * g / w1 * np.sin(w1 * t))
+    k = math.sqrt(-d)
+    return np.exp(-0.5 * g * t) * (np.cosh(k * t) - 0.5 * g / k * np.sinh(k * t))
+
+
+def test_pile_friction_per_mode_from_momentum_autocorrelation():
+    """Eq. (16): gamma_n = max(gamma_0, omega_n) on the fluctuation modes, gamma_0 on the centroid.
+    With V = 0 every mode is a Langevin oscillator of frequency omega_n (omega_0 = 0), so the
+    stationary momentum autocorrelation of mode n is fixed by (omega_n, gamma_n) alone.  hbar is
+    scaled so that omega_P = 20 ps^-1 (omega_n dt <= 0.02: the splitting error is negligible) and
+    gamma_0 = 10 ps^-1 < omega_1 = 15.3 ps^-1, so the two branches of the max differ.  The states
+    start in the stationary distribution (Eq. (7) momenta, free ring-polymer modes).  The other
+    plausible readings (gamma_0 everywhere, 2 omega_n, no centroid friction) miss by > 0.14."""
+    P, n_atoms, steps, lags = 8, 64, 6000, 600
+    T, gamma0, mass = 300.0, 10.0, 4.0
+    prm = rpmd.Params(P=P, temperature=T, dt=0.0005, gamma0=gamma0, seed=9, hbar=P * KB * T / 20.0)
+    masses = np.full(n_atoms, mass)
+    st = rpmd.init_state(np.zeros((n_atoms, 3)), masses, prm)
+
+    def free(xb):
+        return np.zeros(xb.shape[0]), np.zeros_like(xb)
+
+    rec = np.empty((steps, n_atoms * 3, P))
+    for s in range(steps):
+        rpmd.step(st, prm, masses, free)
+        rec[s] = st.Pm.reshape(-1, P)
+    f = np.fft.rfft(rec, n=2 * steps, axis=0)
+    ac = np.fft.irfft(f * np.conj(f), axis=0)[:lags] / (steps - np.arange(lags))[:, None, None]
+    acf = ac.mean(axis=1) / (mass * prm.kT * ACC)          # normalised by the exact <p^2> = m kT
+    t = np.arange(lags) * prm.dt
+    w = prm.omegas()
+    readings = {
+        "paper": np.r_[gamma0, np.maximum(gamma0, w[1:])],
+        "gamma0 everywhere": np.full(P, gamma0),
+        "2 omega_n": np.r_[gamma0, 2.0 * w[1:]],
+        "no centroid friction": np.r_[0.0, np.maximum(gamma0, w[1:])],
+    }
+    dev = {k: np.array([np.max(np.abs(acf[:, n] - _langevin_momentum_acf(t, w[n], g[n]))) for n in range(P)])
+           for k, g in readings.items()}
+    assert np.all(dev["paper"] < 0.07), dev["paper"]
+    for k in ("gamma0 everywhere", "2 omega_n"):
+        assert np.all(dev[k][1:] > 0.14), (k, dev[k])
+    assert dev["no centroid friction"][0] > 0.5, dev["no centroid friction"]
+
+
 def test_centroid_virial_estimator_harmonic_identity():
     """For V = 1/2 k x^2 per dof, -(1/2P) sum_b (x_b - Q_0).F_b = (k/2) sum_{n>0} Q_n^2 exactly
     (x_b - Q_0 = sqrt(P) sum_{n>0} T_bn Q_n and sum_b (x_b - Q_0).Q_0 = 0), so the
@@ -303,3 +358,40 @@ def test_adqtb_simple_adaptation_stays_near_gamma0_on_harmonic_system():
     w = qtb.omega_bins(prm)
     band = (w > 150) & (w < 250)
     assert abs(bath.gamma[0][band].mean() - prm.gamma0) / prm.gamma0 < 0.1
+
+
+def test_simple_adaptation_contracts_at_the_linear_fdt_rate():
+    """Sign and scale of SIMPLE (Eqs. (21)-(23)).  A harmonic oscillator (omega_0) driven by the
+    colored noise of power 2 m gamma(omega) Theta(omega) (Eq. (13)) under the friction gamma_0 has
+    C_vv = 2 gamma Theta w^2 / (m |D|^2) and Re C_vF = 2 gamma gamma_0 Theta w^2 / |D|^2 with
+    D = omega_0^2 - w^2 + i gamma_0 w, so Delta_FDT = 2 gamma Theta w^2 (gamma - gamma_0) / |D|^2:
+    gamma = gamma_0 is the fixed point, and near it one SIMPLE update multiplies gamma - gamma_0
+    by 1 - A_gamma 2 gamma_0 Theta w^2 / |D|^2 (Theta in kcal/mol, A_gamma in ps^-1 per kcal/mol).
+    Starting from gamma = 1.2 gamma_0 (one segment held fixed to reach the stationary state), the
+    measured factor in each resonance bin must match that value and be below one: a flipped sign
+    gives factors above one, a Delta left in amu A^2/ps^2 (no kcal/mol conversion) or a wrong
+    spectrum normalisation moves them far from it."""
+    omega0, n_atoms = 200.0, 300
+    prm = _qtb_prm(n_seg=1024, omega_cut=2825.0, a_gamma=2.0)
+    g0 = prm.gamma0
+    masses = np.full(n_atoms, 1.008)
+    st = rpmd.init_state(np.zeros((n_atoms, 3)), masses, rpmd.Params(P=1, temperature=prm.temperature, dt=prm.dt,
+                                                                       gamma0=g0, seed=prm.seed))
+    bath = qtb.QTB(prm, np.repeat(masses, 3), np.zeros(3 * n_atoms, dtype=int), 1, adapt="none")
+    bath.gamma[:] = 1.2 * g0
+    fn = rpmd.harmonic_forces(omega0, masses)
+    gs = []
+    for s in range(3 * prm.n_seg):
+        qtb.qtb_step(st, masses, bath, fn)
+        if (s + 1) % prm.n_seg == 0:
+            gs.append(bath.gamma[0].copy())
+            bath.adapt = "simple"
+    w = qtb.omega_bins(prm)
+    th = qtb.theta(w, prm.kT, prm.hbar)
+    pred = 1.0 - prm.a_gamma * 2.0 * g0 * th * w ** 2 / ((omega0 ** 2 - w ** 2) ** 2 + g0 ** 2 * w ** 2)
+    band = (w > omega0 - g0) & (w < omega0 + g0)
+    for k in (1, 2):
+        r = (gs[k][band] - g0) / (gs[k - 1][band] - g0)
+        assert np.all(r < 1.0), r
+        np.testing.assert_allclose(r, pred[band], atol=0.07)
+
