@@ -110,7 +110,7 @@ typedef struct {
  * (O, H, H) triples with molecule[i] = i / 3.  pos: [n_atoms][3] initial positions
  * (A), used as the centroids Q_0 (the n = 0 mode of Eq. (4)).  precision: QHP_FP64 or
  * QHP_MIXED.  Allocates nothing on the device until qhp_set_beads.  Returns
- * QHP_ERR_ARG for other layouts.
+ * QHP_ERR_ARG for other layouts and for n_atoms >= 2^26.
  * qhp_destroy_system frees the system's device memory, stream and graphs (the handle is
  * invalid afterwards; NULL is accepted).  Neither has a counterpart in the paper: they
  * are the lifetime of the state the paper's equations act on. */
@@ -301,8 +301,18 @@ int qhp_batch_get_info(qhp_batch batch, qhp_batch_info* out);
 int qhp_batch_get_profile(qhp_batch batch, qhp_profile* out);
 int qhp_autotune(qhp_sys sys, int reps, int* warps_per_atom);
 /* Fix the warps per atom of the mixed pair kernel (1, 2 or 4; 0 = the default for P:
- * 4 if P >= 16, else 1).  Different settings sum the pair forces in different orders. */
+ * 4 if P >= 16, else 1).  The forces do not depend on it: every row is summed in FP32 over
+ * fixed blocks of 32 list entries, each block sum is converted to int64 fixed point once,
+ * and the integers are added, so every setting gives the same bits.
+ *
+ * qhp_set_pair_skip: the mixed pair kernel walks each list row in (partner type, distance)
+ * order and stops a row's group at the first block of entries whose anchor distance exceeds
+ * rc + 2 max|x_ib - A_i| (the largest bead offset from its anchor since the list build):
+ * no bead pair there can come within rc (Sec. III.A.3 lists pairs by centroid, so the list
+ * holds pairs up to rc + skin).  enabled = 0 evaluates every entry instead; the results are
+ * the same bits either way (a verification and measurement hook).  Default 1. */
 int qhp_set_pair_warps(qhp_sys sys, int warps_per_atom);
+int qhp_set_pair_skip(qhp_sys sys, int enabled);
 
 /* Launch mode of qhp_step_rpmd / qhp_step_adqtb.  use_graphs = 1 (default): each
  * step replays one captured CUDA graph whose list-rebuild chain sits behind a

@@ -304,6 +304,18 @@ int qhp_set_pair_warps(qhp_sys s, int warps_per_atom) {
     return QHP_OK;
 }
 
+int qhp_set_pair_skip(qhp_sys s, int enabled) {
+    if (!s || (enabled != 0 && enabled != 1)) {
+        set_error("qhp_set_pair_skip: enabled must be 0 or 1");
+        return QHP_ERR_ARG;
+    }
+    if (s->pair_skip != enabled) {
+        s->pair_skip = enabled;
+        graph_invalidate(s);
+    }
+    return QHP_OK;
+}
+
 int qhp_create_batch(qhp_batch* out, int n_sys, const qhp_sys* systems) {
     if (!out || n_sys < 1 || !systems) {
         set_error("qhp_create_batch: need n_sys >= 1 systems");

@@ -325,6 +325,11 @@ int ensure_capacity(qhp_system_s* s) {
     int64_t row = ((int64_t)(1.25 * (double)longest) + 64 + 7) / 8 * 8;
     if (row > s->N) row = s->N;   // no row is longer than the other atoms
     if (row < 8) row = 8;
+    if (row > LIST_SORT_MAX_ROW) {
+        qhp::set_error("neighbour rows of %lld entries exceed the %d the row sort handles (reduce the skin)",
+                       (long long)row, LIST_SORT_MAX_ROW);
+        return QHP_ERR_ARG;
+    }
     if (row * (int64_t)s->N > ((int64_t)1 << 31) - 1) {
         qhp::set_error("neighbour list too large (%lld rows of %lld entries)", (long long)s->N, (long long)row);
         return QHP_ERR_NOMEM;
@@ -336,6 +341,7 @@ int ensure_capacity(qhp_system_s* s) {
         s->nbr = p;
         s->nbr_cap = row * s->N;
         s->row_cap = (int)row;
+        TRY(list_sort_prepare(s->row_cap));
         std::vector<int> start(s->N + 1);
         for (int i = 0; i <= s->N; ++i) start[i] = i * (int)row;
         QHP_CUDA(cudaMemcpy(s->nbr_start, start.data(), sizeof(int) * (s->N + 1), cudaMemcpyHostToDevice));
@@ -489,6 +495,10 @@ int qhp_create_system(qhp_sys* out, int n_atoms, const int* type, const int* mol
         set_error("n_atoms must be a positive multiple of 3 (O, H, H molecules)");
         return QHP_ERR_ARG;
     }
+    if (n_atoms >= MAX_ATOMS) {
+        set_error("n_atoms must be below %d (the neighbour list's partner index)", MAX_ATOMS);
+        return QHP_ERR_ARG;
+    }
     if (!(box_L > 0.0) || !isfinite(box_L)) {
         set_error("box_L must be positive");
         return QHP_ERR_ARG;
@@ -638,6 +648,7 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     TRY(dalloc(s, &s->cwl, N));
     TRY(dalloc(s, &s->nbr_start, N + 1));
     TRY(dalloc(s, &s->nbr_count, N));
+    TRY(dalloc(s, &s->nbr_nO, N));
     TRY(dalloc(s, &s->e_bond, (size_t)s->n_mol * P));
     TRY(dalloc(s, &s->red_tmp, 1024));
     TRY(dalloc(s, &s->red_out, 256));
@@ -962,7 +973,7 @@ int qhp_get_list_pairs(qhp_sys s, int64_t* pairs, int64_t cap, int64_t* count) {
     int64_t c = 0;
     for (int i = 0; i < N; ++i)
         for (int64_t k = (int64_t)i * s->row_cap; k < (int64_t)i * s->row_cap + cnt[i]; ++k) {
-            const int a = perm[i], b = perm[e[k].x & 0x7fffffff];   // bit 31 flags an H partner
+            const int a = perm[i], b = perm[entry_partner(e[k].x)];
             if (a < b) {
                 if (pairs && c < cap) {
                     pairs[2 * c] = a;

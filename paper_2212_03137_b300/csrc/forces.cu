@@ -28,338 +28,484 @@ namespace qhp {
 
 namespace {
 
+// Coefficients of the two even functions of the DSF Coulomb pair, fitted on [0, rc^2] in
+// t = r^2 (2/rc^2) - 1 (see make_pair_consts): with erfc = 1 - erf,
+//   -V'(r)/r / (q_i q_j k_e) = 1/r^3 - S_c/r - G(r^2),  G(s) = erf(a sqrt s)/s^(3/2) - (2a/sqrt(pi)) e^(-a^2 s)/s,
+//   V(r) / (q_i q_j k_e)     = 1/r - E(r^2) - erfc(a rc)/rc + S_c (r - rc),  E(s) = erf(a sqrt s)/sqrt s.
+// G and E are entire functions of s (their series in a^2 s have no odd powers of r), so a
+// degree-8 polynomial reaches 2.5e-8 of G(0) on the cutoff sphere, below the FP32 rounding of
+// its own evaluation; the pair then needs one special-function operation, the 1/sqrt(r^2).
+constexpr int NPOLY = 9;
+
 struct PairConsts {
-    float rc2, rc, alpha, c2a, sc, ecut, sig2, eps4, eps24, ljshift, L, invL;
+    float rc2, rc, sc, ecut, sig2, eps4, neps24, ljshift, L, invL;
     double rc2_d, rc_d, alpha_d, c2a_d, sc_d, ecut_d, sig2_d, eps4_d, eps24_d, ljshift_d, L_d, invL_d, ke_d;
-    float ke, qO_ke, qH_ke;
-    float p_alpha;        // A&S 7.1.26 p times alpha
-    float neg_a2_log2e;   // -alpha^2 log2(e)
+    float qO_ke, qH_ke;
+    float tscale;           // 2 / rc^2
+    float bucket_lo, bucket_inv;   // the row order's distance buckets (list_bucket)
+    float gpoly[NPOLY];     // G in powers of t
+    float epoly[NPOLY];     // E in powers of t
 };
 
-// List entries carry the partner's sorted index in the low 31 bits and "partner is H"
-// in bit 31, so the partner's charge and LJ flag need no extra load.
-__device__ __forceinline__ int entry_j(int x) { return x & 0x7fffffff; }
-__device__ __forceinline__ bool entry_is_h(int x) { return x < 0; }
+// The partner's sorted index of a list entry (entry_partner); its type rides in bit 31 and
+// its distance bucket in bits 26-30, so neither needs an extra load.
+__device__ __forceinline__ int entry_j(int x) { return entry_partner(x); }
 
-// Hardware approximations of the special-function unit, flush-to-zero (pair distances
-// are never denormal): reciprocal square root (rel. error < 2^-22.9), reciprocal and
-// base-2 exponential (a few ulp), written as PTX so that no range fix-up code surrounds them.
+// Reciprocal square root of the special-function unit, flush-to-zero (pair distances are
+// never denormal), relative error below 2^-22.9, written as PTX so that no range fix-up
+// code surrounds it.
 __device__ __forceinline__ float rsqrt_fast(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float rcp_fast(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float ex2_fast(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
-// erfc(a r) for a r >= 0 with absolute error below 1.5e-7: the rational approximation
-// 7.1.26 of Abramowitz & Stegun (Handbook of Mathematical Functions, 1964; from Hastings),
-// erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1/(1 + p x).
-// The factor exp(-a^2 r^2) is the Gaussian the DSF force needs anyway: it is formed from
-// r^2 directly (exponent -a^2 log2(e) r^2 for the base-2 exponential); gauss receives it.
-__device__ __forceinline__ float erfc_as(float r, float r2, const PairConsts& c, float& gauss) {
-    const float t = rcp_fast(fmaf(c.p_alpha, r, 1.0f));
-    float p = 1.061405429f;
-    p = fmaf(p, t, -1.453152027f);
-    p = fmaf(p, t, 1.421413741f);
-    p = fmaf(p, t, -0.284496736f);
-    p = fmaf(p, t, 0.254829592f);
-    gauss = ex2_fast(c.neg_a2_log2e * r2);
-    return t * p * gauss;
-}
+// Packed FP32x2 arithmetic (one instruction for the two beads a lane carries).
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// One bead pair: DSF Coulomb (+ shifted LJ on O-O), force on i accumulated as -g d.
-template <bool ALL, bool ENERGY>
-__device__ __forceinline__ void pair_term(float dx, float dy, float dz, float qq, bool lj, const PairConsts& c,
-                                          float& fx, float& fy, float& fz, float& en) {
-    if (ALL) {
-        dx -= c.L * rintf(dx * c.invL);
-        dy -= c.L * rintf(dy * c.invL);
-        dz -= c.L * rintf(dz * c.invL);
-    }
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 < c.rc2) {
-        const float rinv = rsqrt_fast(r2);
-        const float r = r2 * rinv;
-        float gauss;
-        const float erfc_ar = erfc_as(r, r2, c, gauss);
-        const float rinv2 = rinv * rinv;
-        // -V'(r)/r = qq (erfc(a r)/r^2 + (2a/sqrt(pi)) e^{-a^2 r^2}/r - S_c) / r
-        float g = qq * fmaf(erfc_ar, rinv2, fmaf(c.c2a * gauss, rinv, -c.sc)) * rinv;
-        float ep = 0.0f;
-        if (ENERGY) ep = qq * (erfc_ar * rinv - c.ecut + c.sc * (r - c.rc));
-        if (lj) {
-            const float s2 = c.sig2 * rinv2;
-            const float s6 = s2 * s2 * s2;
-            g = fmaf(c.eps24 * fmaf(2.0f * s6, s6, -s6), rinv2, g);
-            if (ENERGY) ep += c.eps4 * (s6 * s6 - s6) - c.ljshift;
-        }
-        fx = fmaf(-g, dx, fx);
-        fy = fmaf(-g, dy, fy);
-        fz = fmaf(-g, dz, fz);
-        if (ENERGY) en = fmaf(0.5f, ep, en);
-    }
+// round(x 2^34) as int64, the same value as __float2ll_rn(x * FIX_SCALE_F), for |x| < 2^29,
+// from two 32-bit conversions (64-bit conversions run on the FP64 pipe, which this part has
+// little of).  v = x 2^34 is split exactly into h 2^32 + l with h = floor(v 2^-32) and
+// 0 <= l < 2^32: l is made of v's own mantissa bits, so the FMA forming it is exact, and only
+// l's fraction (below 2^-1 only when |v| < 2^24) is rounded, half to even as for v itself.
+__device__ __forceinline__ long long fix64(float x) {
+    const float v = x * FIX_SCALE_F;
+    const float h = floorf(v * 0x1p-32f);
+    const float l = fmaf(h, -0x1p32f, v);
+    return (long long)((unsigned long long)(unsigned)__float2int_rz(h) << 32) + (long long)__float2uint_rn(l);
 }
 
 constexpr int PAIR_WARPS = 4;   // warps per block
-constexpr int PAIR_RED = PAIR_WARPS * 4 * 64;   // floats of the cross-warp reduction buffer
+constexpr int PAIR_SUB = 32;    // list entries read (and staged) at a time
 
 // Warps that share one atom's list (W): with many beads (P >= 16) four warps split the
-// list; with few beads one warp takes a whole list (32/P entries per iteration) and a
-// block holds four atoms.  This is the default; the autotuner may pick another W.
+// list; with few beads one warp takes a whole list and a block holds four atoms.  This is
+// the default; the autotuner may pick another W.  Forces do not depend on W.
 __host__ __device__ constexpr int pair_warps_default(int P) { return P >= 16 ? 4 : 1; }
 
 struct PairArgs {
     int N, P, W, all;
     const float4* pos;
-    const int *start, *count;
+    const int *start, *count, *nO;
     const int4* nbr;
     const float* charge_s;
     const int *type_s, *perm;
     long long* F;
     float* epair;
     const unsigned* status;
+    const unsigned* dev_max;   // running max |x_ib - A_i|^2 since the list build, or null (no skipping)
     PairConsts c;
 };
 
-// One block (bx) of the pair kernel: APB = PAIR_WARPS / W atoms.  red: PAIR_RED floats.
-template <int P, int W, bool ALL, bool ENERGY>
-__device__ __forceinline__ void pair_body(const PairArgs& A, int bx, float* red_raw) {
-    constexpr int JPW = P >= 32 ? 1 : 32 / P;
-    constexpr int BPL = P > 32 ? P / 32 : 1;
-    constexpr int NB = P > 32 ? P : 32;                   // bead slots reduced across warps
-    constexpr int APB = PAIR_WARPS / W;                   // atoms per block
-    float(*red)[4][NB] = reinterpret_cast<float(*)[4][NB]>(red_raw);
-    const int N = A.N;
-    const float4* __restrict__ pos = A.pos;
-    const int* __restrict__ start = A.start;
-    const int* __restrict__ count = A.count;
-    const int4* __restrict__ nbr = A.nbr;
-    const float* __restrict__ charge_s = A.charge_s;
-    const int* __restrict__ type_s = A.type_s;
-    const int* __restrict__ perm = A.perm;
-    long long* __restrict__ F = A.F;
-    float* __restrict__ epair = A.epair;
-    const PairConsts& c = A.c;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int wa = w % W;                                 // this warp's chunk of the atom's list
-    const int i_raw = bx * APB + w / W;
-    const bool live = i_raw < N;
-    const int i = live ? i_raw : N - 1;                   // idle warps still reach the barrier
-    const int b0 = P >= 32 ? lane : (lane % P);
-    const int jsub = P >= 32 ? 0 : lane / P;
-    const bool ok = live && (*A.status & ST_LIST_OVERFLOW) == 0u;
-    // N * P < 2^30 is checked at set-up, so 32-bit element offsets suffice
-    const float4* __restrict__ pl = pos + b0;
+struct PairSmem {
+    float4 ent[PAIR_WARPS][PAIR_SUB][2];   // staged entries {Dx, Dx, Dy, Dy}, {Dz, Dz, j, -}
+    long long acc[PAIR_WARPS][3][64];      // per warp and bead: int64 sum of the block sums
+    float esum[PAIR_WARPS][64];            // per warp and bead: pair energy (ENERGY)
+};
 
-    float xi[BPL], yi[BPL], zi[BPL], fx[BPL], fy[BPL], fz[BPL], en[BPL];
+// The pair terms of one list entry for the two beads of a lane (Eq. (3)'s V on every bead):
+// DSF Coulomb, plus the shifted LJ when LJ; the force on i, -g d, accumulates in f.  A bead
+// beyond rc adds nothing.  ONE: a single bead (P = 1), carried in .x.
+template <bool LJ, bool ENERGY, bool ONE>
+__device__ __forceinline__ void pair2(float2 dx, float2 dy, float2 dz, float2 qq, const PairConsts& c,
+                                      float2& fx, float2& fy, float2& fz, float2& en) {
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    const bool in0 = r2.x < c.rc2, in1 = !ONE && r2.y < c.rc2;
+    if (in0 || in1) {
+        const float2 rinv = make_float2(rsqrt_fast(r2.x), ONE ? 1.0f : rsqrt_fast(r2.y));
+        const float2 rinv2 = mul2(rinv, rinv);
+        const float2 t = fma2(r2, f2(c.tscale), f2(-1.0f));
+        float2 p = f2(c.gpoly[NPOLY - 1]);
 #pragma unroll
-    for (int u = 0; u < BPL; ++u) {
-        const float4 p = pl[i * P + 32 * u];
-        xi[u] = p.x;
-        yi[u] = p.y;
-        zi[u] = p.z;
-        fx[u] = fy[u] = fz[u] = en[u] = 0.0f;
-    }
-    const float qi = charge_s[i];
-    const bool Oi = type_s[i] == 0;
-    const float qO = qi * c.qO_ke, qH = qi * c.qH_ke;
-    // the list of i is cut into W contiguous chunks, one per warp
-    const int ka = start[i], kb = ok ? ka + count[i] : ka;
-    const int chunk = ((kb - ka + W - 1) / W + JPW - 1) / JPW * JPW;
-    const int kw0 = min(kb, ka + wa * chunk), k1 = min(kb, kw0 + chunk);
-    int k = kw0 + jsub;
-    if (P == 2 || P == 4) {
-        // few beads: little arithmetic per entry, so the loop waits on the list stream and the
-        // dependent position gathers; four entries per lane in flight.  (With P = 1 the extra
-        // registers cost more occupancy than the deeper pipeline gains: measured slower.)
-        for (; k + 3 * JPW < k1; k += 4 * JPW) {
-            int4 e[4];
-            float4 q[4];
+        for (int k = NPOLY - 2; k >= 0; --k) p = fma2(p, t, f2(c.gpoly[k]));
+        // -g = qq (G - 1/r^3 + S_c/r)
+        const float2 u = mul2(rinv, add2(rinv2, f2(-c.sc)));
+        float2 ng = mul2(qq, fma2(u, f2(-1.0f), p));
+        float2 ep = f2(0.0f);
+        if (ENERGY) {
+            float2 pe = f2(c.epoly[NPOLY - 1]);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) e[v] = __ldg(&nbr[k + v * JPW]);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) q[v] = __ldg(&pl[entry_j(e[v].x) * P]);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const bool h = entry_is_h(e[v].x);
-                pair_term<ALL, ENERGY>(__int_as_float(e[v].y) + (q[v].x - xi[0]), __int_as_float(e[v].z) + (q[v].y - yi[0]),
-                                       __int_as_float(e[v].w) + (q[v].z - zi[0]), h ? qH : qO, Oi && !h, c, fx[0], fy[0],
-                                       fz[0], en[0]);
-            }
+            for (int k = NPOLY - 2; k >= 0; --k) pe = fma2(pe, t, f2(c.epoly[k]));
+            const float2 r = mul2(r2, rinv);
+            ep = mul2(qq, add2(add2(rinv, fma2(pe, f2(-1.0f), f2(-c.ecut))), mul2(f2(c.sc), add2(r, f2(-c.rc)))));
         }
+        if (LJ) {
+            const float2 s2 = mul2(f2(c.sig2), rinv2);
+            const float2 s6 = mul2(mul2(s2, s2), s2);
+            // -24 eps (2 s^12 - s^6) / r^2
+            ng = fma2(mul2(f2(c.neps24), rinv2), mul2(s6, fma2(s6, f2(2.0f), f2(-1.0f))), ng);
+            if (ENERGY) ep = add2(ep, fma2(f2(c.eps4), mul2(s6, add2(s6, f2(-1.0f))), f2(-c.ljshift)));
+        }
+        if (!in0) ng.x = 0.0f, ep.x = 0.0f;
+        if (!in1) ng.y = 0.0f, ep.y = 0.0f;
+        fx = fma2(ng, dx, fx);
+        fy = fma2(ng, dy, fy);
+        fz = fma2(ng, dz, fz);
+        if (ENERGY) en = fma2(f2(0.5f), ep, en);
     }
-    if (P >= 32) {
-        // all lanes walk the same entry: the warp's entries are staged in shared memory 32 at
-        // a time by asynchronous copies issued one block ahead, so that only the dependent
-        // position gather is left on the loop's critical path.  Same entry order and pairing
-        // as the loop below, hence the same sums.
-        __shared__ int4 s_e[PAIR_WARPS][2][32];
-        int4(*ring)[32] = s_e[w];
-        const auto stage = [&](int kb0, int slot) {
-            const int kk = kb0 + lane;
-            const bool in = kk < k1;
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(&ring[slot][lane]);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(nbr + (in ? kk : kb0)),
-                         "r"(in ? 16 : 0)
-                         : "memory");
-        };
-        int slot = 0;
-        if (k < k1) stage(k, 0);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        for (int kb0 = k; kb0 < k1; kb0 += 32, slot ^= 1) {
-            if (kb0 + 32 < k1) stage(kb0 + 32, slot ^ 1);
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this block's copies are done
-            __syncwarp();
-            const int n = min(32, k1 - kb0);
-            int q = 0;
-            for (; q + 1 < n; q += 2) {
-                const int4 e0 = ring[slot][q];
-                const int4 e1 = ring[slot][q + 1];
-                const int j0 = entry_j(e0.x) * P, j1 = entry_j(e1.x) * P;
-                const bool h0 = entry_is_h(e0.x), h1 = entry_is_h(e1.x);
+}
+
+// The partner's two beads of lane bp: the xy plane's float4 and the z plane's float2
+// (bead_word layout); one bead (P = 1) is carried in .x and .y alike.
+template <int P>
+__device__ __forceinline__ void load_pair_beads(const float* __restrict__ pw, int j, int bp, float2& x, float2& y,
+                                                float2& z) {
+    if (P == 1) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(pw) + j);
+        x = f2(q.x), y = f2(q.y), z = f2(q.z);
+    } else {
+        const float* rec = pw + (size_t)j * bead_stride(P);
+        const float4 q = __ldg(reinterpret_cast<const float4*>(rec) + bp);
+        x = make_float2(q.x, q.y), y = make_float2(q.z, q.w);
+        z = __ldg(reinterpret_cast<const float2*>(rec + 2 * P) + bp);
+    }
+}
+
+// The same terms for a single bead (P = 1) in scalar FP32.
+template <bool LJ, bool ENERGY>
+__device__ __forceinline__ void pair1(float dx, float dy, float dz, float qq, const PairConsts& c, float& fx, float& fy,
+                                      float& fz, float& en) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 < c.rc2) {
+        const float rinv = rsqrt_fast(r2);
+        const float rinv2 = rinv * rinv;
+        const float t = fmaf(r2, c.tscale, -1.0f);
+        float p = c.gpoly[NPOLY - 1];
 #pragma unroll
-                for (int u = 0; u < BPL; ++u) {
-                    const float4 a = __ldg(&pl[j0 + 32 * u]);
-                    const float4 b = __ldg(&pl[j1 + 32 * u]);
-                    pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
-                                           __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u],
-                                           fy[u], fz[u], en[u]);
-                    pair_term<ALL, ENERGY>(__int_as_float(e1.y) + (b.x - xi[u]), __int_as_float(e1.z) + (b.y - yi[u]),
-                                           __int_as_float(e1.w) + (b.z - zi[u]), h1 ? qH : qO, Oi && !h1, c, fx[u],
-                                           fy[u], fz[u], en[u]);
+        for (int k = NPOLY - 2; k >= 0; --k) p = fmaf(p, t, c.gpoly[k]);
+        float ng = qq * fmaf(rinv, c.sc - rinv2, p);   // qq (G - 1/r^3 + S_c/r)
+        float ep = 0.0f;
+        if (ENERGY) {
+            float pe = c.epoly[NPOLY - 1];
+#pragma unroll
+            for (int k = NPOLY - 2; k >= 0; --k) pe = fmaf(pe, t, c.epoly[k]);
+            ep = qq * (rinv - pe - c.ecut + c.sc * (r2 * rinv - c.rc));
+        }
+        if (LJ) {
+            const float s2 = c.sig2 * rinv2;
+            const float s6 = s2 * s2 * s2;
+            ng = fmaf(c.neps24 * rinv2, s6 * fmaf(s6, 2.0f, -1.0f), ng);
+            if (ENERGY) ep += fmaf(c.eps4, s6 * (s6 - 1.0f), -c.ljshift);
+        }
+        fx = fmaf(ng, dx, fx);
+        fy = fmaf(ng, dy, fy);
+        fz = fmaf(ng, dz, fz);
+        if (ENERGY) en = fmaf(0.5f, ep, en);
+    }
+}
+
+// One list entry for a single bead: partner position p, anchor separation D.
+template <bool ALL, bool LJ, bool ENERGY>
+__device__ __forceinline__ void pair_entry1(float Dx, float Dy, float Dz, float4 p, float2 nxi, float2 nyi, float2 nzi,
+                                            float qq, const PairConsts& c, float2& fx, float2& fy, float2& fz, float2& en) {
+    float dx = Dx + (p.x + nxi.x), dy = Dy + (p.y + nyi.x), dz = Dz + (p.z + nzi.x);
+    if (ALL) {
+        dx = fmaf(-c.L, rintf(dx * c.invL), dx);
+        dy = fmaf(-c.L, rintf(dy * c.invL), dy);
+        dz = fmaf(-c.L, rintf(dz * c.invL), dz);
+    }
+    pair1<LJ, ENERGY>(dx, dy, dz, qq, c, fx.x, fy.x, fz.x, en.x);
+}
+
+// One list entry (anchor separation D) for the lane's two beads, the partner's beads given.
+template <int P, bool ALL, bool LJ, bool ENERGY>
+__device__ __forceinline__ void pair_entry_at(float2 Dx, float2 Dy, float2 Dz, float2 px, float2 py, float2 pz,
+                                              float2 nxi, float2 nyi, float2 nzi, float2 qq, const PairConsts& c,
+                                              float2& fx, float2& fy, float2& fz, float2& en) {
+    // d = D_ij + (x_jb - x_ib): anchor separation plus the two bead offsets
+    float2 dx = add2(add2(px, nxi), Dx);
+    float2 dy = add2(add2(py, nyi), Dy);
+    float2 dz = add2(add2(pz, nzi), Dz);
+    if (ALL) {   // small boxes: minimum image per bead pair
+        dx = fma2(f2(-c.L), make_float2(rintf(dx.x * c.invL), rintf(dx.y * c.invL)), dx);
+        dy = fma2(f2(-c.L), make_float2(rintf(dy.x * c.invL), rintf(dy.y * c.invL)), dy);
+        dz = fma2(f2(-c.L), make_float2(rintf(dz.x * c.invL), rintf(dz.y * c.invL)), dz);
+    }
+    pair2<LJ, ENERGY, P == 1>(dx, dy, dz, qq, c, fx, fy, fz, en);
+}
+
+// One list entry (anchor separation D, partner j) for the lane's two beads.
+template <int P, bool ALL, bool LJ, bool ENERGY>
+__device__ __forceinline__ void pair_entry(float2 Dx, float2 Dy, float2 Dz, int j, const float* __restrict__ pw,
+                                           int bp, float2 nxi, float2 nyi, float2 nzi, float2 qq, const PairConsts& c,
+                                           float2& fx, float2& fy, float2& fz, float2& en) {
+    float2 px, py, pz;
+    load_pair_beads<P>(pw, j, bp, px, py, pz);
+    pair_entry_at<P, ALL, LJ, ENERGY>(Dx, Dy, Dz, px, py, pz, nxi, nyi, nzi, qq, c, fx, fy, fz, en);
+}
+
+// Entries per deterministic partial sum: 32, or for few beads as many as make eight entries
+// per lane (32 with one lane per entry, P <= 2), so that the per-block reduction stays a small
+// share of the work.
+__host__ __device__ constexpr int pair_block(int P) { return P >= 16 ? 32 : (P <= 2 ? 1024 : 512 / P); }
+
+// Per-warp state of one atom's row walk.
+struct PairLane {
+    float2 nxi, nyi, nzi;   // minus the lane's own two bead offsets
+    int i, slot, bp, b_stop;
+};
+
+// Adds the FP32 sums (fx, fy, fz) of one block to the warp's int64 accumulators: the slots
+// first in a fixed tree, then one int64 conversion per value; value v = (dim v % 3, bead
+// 2 bp + v / 3), slot s < S takes values s R .. s R + R - 1, chosen by a select so that every
+// lane runs the same R conversions.
+template <int P>
+__device__ __forceinline__ void pair_block_sum(float2 fx, float2 fy, float2 fz, int slot, int bp, long long (*acc)[64]) {
+    constexpr int LPE = P == 1 ? 1 : P / 2;
+    constexpr int EPI = 32 / LPE;
+#pragma unroll
+    for (int off = LPE; off < 32; off <<= 1) {
+        fx.x += __shfl_xor_sync(0xffffffffu, fx.x, off);
+        fx.y += __shfl_xor_sync(0xffffffffu, fx.y, off);
+        fy.x += __shfl_xor_sync(0xffffffffu, fy.x, off);
+        fy.y += __shfl_xor_sync(0xffffffffu, fy.y, off);
+        fz.x += __shfl_xor_sync(0xffffffffu, fz.x, off);
+        fz.y += __shfl_xor_sync(0xffffffffu, fz.y, off);
+    }
+    const float vals[6] = {fx.x, fy.x, fz.x, fx.y, fy.y, fz.y};
+    constexpr int NV = P == 1 ? 3 : 6;
+    constexpr int S = EPI < NV ? EPI : NV;
+    constexpr int R = (NV + S - 1) / S;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = slot * R + r;
+        float x = vals[r];
+#pragma unroll
+        for (int s2 = 1; s2 < S; ++s2)
+            if (s2 * R + r < NV) x = (slot == s2) ? vals[s2 * R + r] : x;
+        if (slot < S && v < NV) acc[v % 3][2 * bp + v / 3] += fix64(x);
+    }
+}
+
+// The blocks of one group of atom i's row, [k_begin, k_end), that belong to this warp: the
+// first is block `first` of the group, then every W-th.  Entries are read 32 at a time (lane
+// k: entry k); when several lanes share an entry it is staged in shared memory, and slots past
+// the group's end hold a dummy partner (atom i itself, L/2 away in each dimension: beyond rc
+// in every image), so every iteration runs unchecked.  Within the group entries come by |D|^2
+// bucket: at the first 32 entries that all lie beyond reach the group ends for this warp.
+template <int P, int W, bool ALL, bool LJ, bool ENERGY>
+__device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L, int k_begin, int k_end, int first,
+                                           float qqs, float4 (*ent)[2], long long (*acc)[64], float2& en) {
+    constexpr int LPE = P == 1 ? 1 : P / 2;
+    constexpr int EPI = 32 / LPE;
+    constexpr int BLK = pair_block(P);
+    const PairConsts& c = A.c;
+    const float* __restrict__ pw = reinterpret_cast<const float*>(A.pos);
+    const int lane = threadIdx.x & 31;
+    const float2 qq = f2(qqs);
+    for (int kb = k_begin + first * BLK; kb < k_end; kb += W * BLK) {
+        const int bend = min(k_end, kb + BLK);
+        float2 fx = f2(0.0f), fy = f2(0.0f), fz = f2(0.0f);
+        bool beyond = false;
+        if (LPE == 1) {
+            // one lane per entry, two entries per lane in flight: 64 entries at a time (a lane
+            // still adds its entries in index order), both partners gathered before either is used
+            for (int sb = kb; sb < bend; sb += 64) {
+                const int n0 = min(32, bend - sb), n1 = min(32, bend - sb - 32);
+                int4 e0 = make_int4(0, 0, 0, 0), e1 = make_int4(0, 0, 0, 0);
+                bool a0 = false, a1 = false;
+                if (lane < n0) {
+                    e0 = __ldg(&A.nbr[sb + lane]);
+                    a0 = entry_bucket(e0.x) < L.b_stop;
+                }
+                if (lane < n1) {
+                    e1 = __ldg(&A.nbr[sb + 32 + lane]);
+                    a1 = entry_bucket(e1.x) < L.b_stop;
+                }
+                const unsigned am0 = __ballot_sync(0xffffffffu, a0);
+                const unsigned am1 = __ballot_sync(0xffffffffu, a1);
+                if (am0 == 0u) {
+                    beyond = true;
+                    break;
+                }
+                if (P == 1) {
+                    const float4 p0 = __ldg(reinterpret_cast<const float4*>(pw) + (a0 ? entry_j(e0.x) : L.i));
+                    const float4 p1 = __ldg(reinterpret_cast<const float4*>(pw) + (a1 ? entry_j(e1.x) : L.i));
+                    if (a0)
+                        pair_entry1<ALL, LJ, ENERGY>(__int_as_float(e0.y), __int_as_float(e0.z), __int_as_float(e0.w), p0, L.nxi,
+                                                     L.nyi, L.nzi, qqs, c, fx, fy, fz, en);
+                    if (a1)
+                        pair_entry1<ALL, LJ, ENERGY>(__int_as_float(e1.y), __int_as_float(e1.z), __int_as_float(e1.w), p1, L.nxi,
+                                                     L.nyi, L.nzi, qqs, c, fx, fy, fz, en);
+                } else {
+                    float2 px0, py0, pz0, px1, py1, pz1;
+                    load_pair_beads<P>(pw, a0 ? entry_j(e0.x) : L.i, L.bp, px0, py0, pz0);
+                    load_pair_beads<P>(pw, a1 ? entry_j(e1.x) : L.i, L.bp, px1, py1, pz1);
+                    if (a0)
+                        pair_entry_at<P, ALL, LJ, ENERGY>(f2(__int_as_float(e0.y)), f2(__int_as_float(e0.z)), f2(__int_as_float(e0.w)),
+                                                          px0, py0, pz0, L.nxi, L.nyi, L.nzi, qq, c, fx, fy, fz, en);
+                    if (a1)
+                        pair_entry_at<P, ALL, LJ, ENERGY>(f2(__int_as_float(e1.y)), f2(__int_as_float(e1.z)), f2(__int_as_float(e1.w)),
+                                                          px1, py1, pz1, L.nxi, L.nyi, L.nzi, qq, c, fx, fy, fz, en);
+                }
+                if (am1 == 0u && n1 > 0) {   // the second 32 and all after them lie beyond reach
+                    beyond = true;
+                    break;
                 }
             }
-            if (q < n) {
-                const int4 e0 = ring[slot][q];
-                const int j0 = entry_j(e0.x) * P;
-                const bool h0 = entry_is_h(e0.x);
-#pragma unroll
-                for (int u = 0; u < BPL; ++u) {
-                    const float4 a = __ldg(&pl[j0 + 32 * u]);
-                    pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
-                                           __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u],
-                                           fy[u], fz[u], en[u]);
+        } else {
+            for (int sb = kb; sb < bend; sb += 32) {
+                const int n = min(32, bend - sb);
+                int4 e = make_int4(0, 0, 0, 0);
+                bool active = false;
+                if (lane < n) {
+                    e = __ldg(&A.nbr[sb + lane]);
+                    active = entry_bucket(e.x) < L.b_stop;
+                }
+                const unsigned am = __ballot_sync(0xffffffffu, active);
+                if (am == 0u) {
+                    beyond = true;
+                    break;
+                }
+                const int nit = (__popc(am) + EPI - 1) / EPI;   // active entries form a prefix (bucket order)
+                const float dx = lane < n ? __int_as_float(e.y) : 0.5f * c.L;
+                const float dy = lane < n ? __int_as_float(e.z) : 0.5f * c.L;
+                const float dz = lane < n ? __int_as_float(e.w) : 0.5f * c.L;
+                __syncwarp();
+                ent[lane][0] = make_float4(dx, dx, dy, dy);
+                ent[lane][1] = make_float4(dz, dz, __int_as_float(lane < n ? entry_j(e.x) : L.i), 0.0f);
+                __syncwarp();
+                for (int it = 0; it < nit; ++it) {
+                    const float4 a = ent[it * EPI + L.slot][0], b = ent[it * EPI + L.slot][1];
+                    pair_entry<P, ALL, LJ, ENERGY>(make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                                   __float_as_int(b.z), pw, L.bp, L.nxi, L.nyi, L.nzi, qq, c, fx, fy, fz, en);
                 }
             }
-            __syncwarp();   // every lane is done with this slot before it is refilled
         }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        k = k1;
+        pair_block_sum<P>(fx, fy, fz, L.slot, L.bp, acc);
+        if (beyond) break;
     }
-    // two list entries per iteration: both entries and all their loads are in flight together
-    for (; k + JPW < k1; k += 2 * JPW) {
-        const int4 e0 = __ldg(&nbr[k]);
-        const int4 e1 = __ldg(&nbr[k + JPW]);
-        const int j0 = entry_j(e0.x) * P, j1 = entry_j(e1.x) * P;
-        const bool h0 = entry_is_h(e0.x), h1 = entry_is_h(e1.x);
-#pragma unroll
-        for (int u = 0; u < BPL; ++u) {
-            const float4 a = __ldg(&pl[j0 + 32 * u]);
-            const float4 b = __ldg(&pl[j1 + 32 * u]);
-            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
-                                   __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u], fy[u],
-                                   fz[u], en[u]);
-            pair_term<ALL, ENERGY>(__int_as_float(e1.y) + (b.x - xi[u]), __int_as_float(e1.z) + (b.y - yi[u]),
-                                   __int_as_float(e1.w) + (b.z - zi[u]), h1 ? qH : qO, Oi && !h1, c, fx[u], fy[u],
-                                   fz[u], en[u]);
-        }
+}
+
+// One block (bx) of the pair kernel: APB = PAIR_WARPS / W atoms, W warps per atom.
+//
+// Lanes: with P >= 2 a lane carries beads 2bp and 2bp + 1 of one list entry (LPE = P/2 lanes
+// per entry) and a warp takes EPI = 64/P entries at a time; with P = 1 a lane takes one entry.
+// The row of atom i holds its O partners first, then its H partners (k_list_sort), so the
+// charge product and the LJ switch are fixed within each group.  Each group is cut into
+// blocks of pair_block(P) entries; block q of the row (O blocks first) belongs to warp q mod W.
+// A block's FP32 sum is converted to int64 once and the integers are added, so the forces do
+// not depend on W.  Entries beyond rc + 2 max|x_ib - A_i| (+ margin) of every bead pair are
+// skipped (pair_group): they would add exactly zero.
+template <int P, int W, bool ALL, bool ENERGY>
+__device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& sm) {
+    constexpr bool ONE = P == 1;
+    constexpr int LPE = ONE ? 1 : P / 2;
+    constexpr int APB = PAIR_WARPS / W;
+    constexpr int BLK = pair_block(P);
+    const PairConsts& c = A.c;
+    const float* __restrict__ pw = reinterpret_cast<const float*>(A.pos);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int wa = w % W;
+    const int i_raw = bx * APB + w / W;
+    const bool live = i_raw < A.N;
+    PairLane L;
+    L.i = live ? i_raw : A.N - 1;      // idle warps still reach the barrier
+    L.slot = lane / LPE;
+    L.bp = lane % LPE;
+    const int i = L.i, slot = L.slot, bp = L.bp;
+    const bool ok = live && (*A.status & ST_LIST_OVERFLOW) == 0u;
+    load_pair_beads<P>(pw, i, bp, L.nxi, L.nyi, L.nzi);
+    L.nxi = make_float2(-L.nxi.x, -L.nxi.y), L.nyi = make_float2(-L.nyi.x, -L.nyi.y);
+    L.nzi = make_float2(-L.nzi.x, -L.nzi.y);
+    const float qi = A.charge_s[i];
+    const bool Oi = A.type_s[i] == 0;
+    if (slot == 0) {
+        sm.acc[w][0][2 * bp] = sm.acc[w][1][2 * bp] = sm.acc[w][2][2 * bp] = 0;
+        sm.acc[w][0][2 * bp + 1] = sm.acc[w][1][2 * bp + 1] = sm.acc[w][2][2 * bp + 1] = 0;
     }
-    if (k < k1) {
-        const int4 e0 = __ldg(&nbr[k]);
-        const int j0 = entry_j(e0.x) * P;
-        const bool h0 = entry_is_h(e0.x);
-#pragma unroll
-        for (int u = 0; u < BPL; ++u) {
-            const float4 a = __ldg(&pl[j0 + 32 * u]);
-            pair_term<ALL, ENERGY>(__int_as_float(e0.y) + (a.x - xi[u]), __int_as_float(e0.z) + (a.y - yi[u]),
-                                   __int_as_float(e0.w) + (a.z - zi[u]), h0 ? qH : qO, Oi && !h0, c, fx[u], fy[u],
-                                   fz[u], en[u]);
-        }
-    }
-    if (P < 32) {
-#pragma unroll
-        for (int off = (P < 32 ? P : 16); off < 32; off <<= 1) {
-            fx[0] += __shfl_xor_sync(0xffffffffu, fx[0], off);
-            fy[0] += __shfl_xor_sync(0xffffffffu, fy[0], off);
-            fz[0] += __shfl_xor_sync(0xffffffffu, fz[0], off);
-            if (ENERGY) en[0] += __shfl_xor_sync(0xffffffffu, en[0], off);
-        }
-    }
-    if (jsub == 0) {
-#pragma unroll
-        for (int u = 0; u < BPL; ++u) {
-            const int b = b0 + 32 * u;
-            red[w][0][b] = fx[u];
-            red[w][1][b] = fy[u];
-            red[w][2][b] = fz[u];
-            red[w][3][b] = en[u];
+    // first bucket beyond reach of any bead pair (LIST_BUCKETS + 2: none is skipped)
+    L.b_stop = LIST_BUCKETS + 2;
+    if (!ALL && A.dev_max) {
+        const float m2 = __uint_as_float(*A.dev_max);
+        if (m2 >= 0.0f && m2 <= 1.0e4f) {
+            const float reach = c.rc + 2.0f * sqrtf(m2) * 1.000001f + 1.0e-3f;
+            L.b_stop = list_bucket_d2(reach * reach, c.bucket_lo, c.bucket_inv) + 1;   // above reach's own bucket
         }
     }
-    __syncthreads();
-    // the first warp of each atom adds the chunks in a fixed order and writes each bead force once
-    if (live && wa == 0 && jsub == 0) {
-        const int a = perm[i];
+    const int ka = A.start[i];
+    const int cnt = ok ? A.count[i] : 0;
+    const int nO = ok ? min(A.nO[i], cnt) : 0;
+    float2 en = f2(0.0f);
+    // O partners: blocks wa, wa + W, ... of the group; H partners: numbered after the O blocks
+    if (Oi) pair_group<P, W, ALL, true, ENERGY>(A, L, ka, ka + nO, wa, qi * c.qO_ke, sm.ent[w], sm.acc[w], en);
+    else pair_group<P, W, ALL, false, ENERGY>(A, L, ka, ka + nO, wa, qi * c.qO_ke, sm.ent[w], sm.acc[w], en);
+    const int nb0 = (nO + BLK - 1) / BLK;
+    pair_group<P, W, ALL, false, ENERGY>(A, L, ka + nO, ka + cnt, ((wa - nb0 % W) + W) % W, qi * c.qH_ke, sm.ent[w],
+                                         sm.acc[w], en);
+    if (ENERGY) {
 #pragma unroll
-        for (int u = 0; u < BPL; ++u) {
-            const int b = b0 + 32 * u;
-            float sx = red[w][0][b], sy = red[w][1][b], sz = red[w][2][b], se = red[w][3][b];
+        for (int off = LPE; off < 32; off <<= 1) {
+            en.x += __shfl_xor_sync(0xffffffffu, en.x, off);
+            en.y += __shfl_xor_sync(0xffffffffu, en.y, off);
+        }
+        if (slot == 0) {
+            sm.esum[w][2 * bp] = en.x;
+            if (!ONE) sm.esum[w][2 * bp + 1] = en.y;
+        }
+    }
+    if (W > 1) __syncthreads();
+    else __syncwarp();
+    // the first warp of each atom adds the W integer sums and writes each bead force once
+    if (live && wa == 0 && slot == 0) {
+        const int a = A.perm[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            long long s0 = sm.acc[w][d][2 * bp], s1 = ONE ? 0 : sm.acc[w][d][2 * bp + 1];
 #pragma unroll
             for (int v = 1; v < W; ++v) {
-                sx += red[w + v][0][b];
-                sy += red[w + v][1][b];
-                sz += red[w + v][2][b];
-                se += red[w + v][3][b];
+                s0 += sm.acc[w + v][d][2 * bp];
+                if (!ONE) s1 += sm.acc[w + v][d][2 * bp + 1];
             }
-            F[((size_t)a * 3 + 0) * P + b] = __float2ll_rn(sx * FIX_SCALE_F);
-            F[((size_t)a * 3 + 1) * P + b] = __float2ll_rn(sy * FIX_SCALE_F);
-            F[((size_t)a * 3 + 2) * P + b] = __float2ll_rn(sz * FIX_SCALE_F);
-            if (ENERGY) epair[(size_t)i * P + b] = se;
+            long long* out = A.F + ((size_t)a * 3 + d) * P + 2 * bp;
+            if (ONE) out[0] = s0;
+            else *reinterpret_cast<longlong2*>(out) = make_longlong2(s0, s1);
+        }
+        if (ENERGY) {
+            float e0 = sm.esum[w][2 * bp], e1 = ONE ? 0.0f : sm.esum[w][2 * bp + 1];
+#pragma unroll
+            for (int v = 1; v < W; ++v) {
+                e0 += sm.esum[w + v][2 * bp];
+                if (!ONE) e1 += sm.esum[w + v][2 * bp + 1];
+            }
+            A.epair[(size_t)i * P + 2 * bp] = e0;
+            if (!ONE) A.epair[(size_t)i * P + 2 * bp + 1] = e1;
         }
     }
 }
 
-// Residency: with P = 16 or 32 (one atom per block, lanes = beads) the loop is latency bound
-// and 16 resident blocks (64 warps, 32 registers a thread) measured 12% faster than 10-12
-// (with the staged entries of P = 32: 0.300 ms at 16 blocks, 0.318 ms at 12); with few
-// beads the compiler's default allocation (minimum 0) is faster, and P = 64 (two beads a
-// lane) would spill.
+// Residency: with two beads per lane the loop holds twice the scalar state, and the compiler's
+// choice (48-62 registers, 8-10 blocks per SM) left the gathers' latency exposed; 12 blocks
+// (40 registers, a few spilled words) measured 5-10% faster at P = 32.  P <= 2 keep the
+// compiler's allocation.
 template <int P>
-__host__ __device__ constexpr int pair_min_blocks() { return (P == 16 || P == 32) ? 16 : 0; }
+__host__ __device__ constexpr int pair_min_blocks() { return P >= 4 ? 12 : 0; }
 
 template <int P, int W, bool ALL, bool ENERGY>
 __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_min_blocks<P>()) k_pair_mixed(const __grid_constant__ PairArgs A) {
-    __shared__ float red[PAIR_RED];
-    pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, red);
+    __shared__ PairSmem sm;
+    pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, sm);
 }
 
 // Batched systems: one persistent launch per (bead count, small-box path, warps per atom)
 // present, over the (system, block) items of the systems of that kind.  Each launch carries
 // one specialisation, so it runs at that specialisation's registers and residency (the same
 // as the single-system kernel).
-// The persistent item loop keeps a few more values live than the single-system kernel:
-// 12 resident blocks (40 registers) for P = 16 and 32 instead of 16.
 template <int P>
-__host__ __device__ constexpr int pair_batch_min_blocks() { return (P == 16 || P == 32) ? 12 : 0; }
+__host__ __device__ constexpr int pair_batch_min_blocks() { return 0; }
 
 template <int P, int W, bool ALL>
 __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_batch_min_blocks<P>()) k_pair_batch(const PairArgs* __restrict__ args,
                                                                                       const int2* __restrict__ items,
                                                                                       const int* __restrict__ ranges) {
-    __shared__ float red[PAIR_RED];
+    __shared__ PairSmem sm;
     for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
         const int2 w = items[it];
-        __syncthreads();   // the previous item's reduction has been read
-        pair_body<P, W, ALL, false>(args[w.x], w.y, red);
+        __syncthreads();   // the previous item's sums have been read
+        pair_body<P, W, ALL, false>(args[w.x], w.y, sm);
     }
 }
 
@@ -551,7 +697,10 @@ __device__ __forceinline__ void bonded_body(const BondArgs& A, int t) {
     const int sO = iperm[aO], s1 = iperm[aH1], s2 = iperm[aH2];
     if (MIXED) {
         float d1[3], d2[3];
-        const float4 xo = pos_f[(size_t)sO * P + b], x1 = pos_f[(size_t)s1 * P + b], x2 = pos_f[(size_t)s2 * P + b];
+        const float* pw = reinterpret_cast<const float*>(pos_f);
+        const float3 xo = make_float3(pw[bead_word(sO, b, 0, P)], pw[bead_word(sO, b, 1, P)], pw[bead_word(sO, b, 2, P)]);
+        const float3 x1 = make_float3(pw[bead_word(s1, b, 0, P)], pw[bead_word(s1, b, 1, P)], pw[bead_word(s1, b, 2, P)]);
+        const float3 x2 = make_float3(pw[bead_word(s2, b, 0, P)], pw[bead_word(s2, b, 1, P)], pw[bead_word(s2, b, 2, P)]);
         const float4 a1 = reinterpret_cast<const float4*>(dA)[(size_t)m * 2 + 0];
         const float4 a2 = reinterpret_cast<const float4*>(dA)[(size_t)m * 2 + 1];
         d1[0] = (x1.x - xo.x) + a1.x;
@@ -648,10 +797,10 @@ __global__ void k_count_pairs(int N, int P, int mixed, int all, const float4* __
             if (j <= i) continue;
             double r2;
             if (mixed) {
-                const float4 pj = pos_f[(size_t)j * P + b], pi = pos_f[(size_t)i * P + b];
-                float dx = __int_as_float(e.y) + (pj.x - pi.x);
-                float dy = __int_as_float(e.z) + (pj.y - pi.y);
-                float dz = __int_as_float(e.w) + (pj.z - pi.z);
+                const float* pw = reinterpret_cast<const float*>(pos_f);
+                float dx = __int_as_float(e.y) + (pw[bead_word(j, b, 0, P)] - pw[bead_word(i, b, 0, P)]);
+                float dy = __int_as_float(e.z) + (pw[bead_word(j, b, 1, P)] - pw[bead_word(i, b, 1, P)]);
+                float dz = __int_as_float(e.w) + (pw[bead_word(j, b, 2, P)] - pw[bead_word(i, b, 2, P)]);
                 if (all) {
                     dx -= c.L * rintf(dx * c.invL);
                     dy -= c.L * rintf(dy * c.invL);
@@ -674,6 +823,60 @@ __global__ void k_count_pairs(int N, int P, int mixed, int all, const float4* __
     }
     atomicAdd(&out2[0], n);
     atomicAdd(&out2[1], noo);
+}
+
+// Degree NPOLY - 1 interpolant of f(t) on [-1, 1] at the NPOLY Chebyshev nodes, in powers of t.
+template <class Fn>
+void chebyshev_fit(Fn f, float* out) {
+    constexpr int n = NPOLY;
+    double cc[n];
+    for (int k = 0; k < n; ++k) {
+        double sum = 0.0;
+        for (int m = 0; m < n; ++m) {
+            const double th = M_PI * (m + 0.5) / n;
+            sum += f(cos(th)) * cos(k * th);
+        }
+        cc[k] = (k == 0 ? 1.0 : 2.0) * sum / n;
+    }
+    double T[n][n] = {};   // T[k][p]: coefficient of t^p in the Chebyshev polynomial T_k
+    T[0][0] = 1.0;
+    T[1][1] = 1.0;
+    for (int k = 2; k < n; ++k)
+        for (int p = 0; p < n; ++p) T[k][p] = (p > 0 ? 2.0 * T[k - 1][p - 1] : 0.0) - T[k - 2][p];
+    for (int p = 0; p < n; ++p) {
+        double sum = 0.0;
+        for (int k = 0; k < n; ++k) sum += cc[k] * T[k][p];
+        out[p] = (float)sum;
+    }
+}
+
+// G(s) = erf(a sqrt s)/s^(3/2) - (2a/sqrt(pi)) e^(-a^2 s)/s and E(s) = erf(a sqrt s)/sqrt s, with
+// their power series in x = a^2 s (G = a^3 (4/sqrt(pi)) sum (-x)^m/(m!(2m+3)),
+// E = a (2/sqrt(pi)) sum (-x)^m/(m!(2m+1))) where the closed forms cancel.
+double dsf_G(double a, double s) {
+    const double x = a * a * s;
+    if (x < 0.5) {
+        double sum = 0.0, term = 1.0;
+        for (int m = 0; m < 20; ++m) {
+            sum += term / (2 * m + 3);
+            term *= -x / (m + 1);
+        }
+        return a * a * a * 4.0 / sqrt(M_PI) * sum;
+    }
+    const double r = sqrt(s);
+    return erf(a * r) / (s * r) - 2.0 * a / sqrt(M_PI) * exp(-x) / s;
+}
+double dsf_E(double a, double s) {
+    const double x = a * a * s;
+    if (x < 0.5) {
+        double sum = 0.0, term = 1.0;
+        for (int m = 0; m < 20; ++m) {
+            sum += term / (2 * m + 1);
+            term *= -x / (m + 1);
+        }
+        return a * 2.0 / sqrt(M_PI) * sum;
+    }
+    return erf(a * sqrt(s)) / sqrt(s);
 }
 
 PairConsts make_pair_consts(const qhp_system_s* s) {
@@ -699,21 +902,21 @@ PairConsts make_pair_consts(const qhp_system_s* s) {
     c.ke_d = COULOMB;
     c.rc2 = (float)c.rc2_d;
     c.rc = (float)rc;
-    c.alpha = (float)a;
-    c.c2a = (float)c.c2a_d;
     c.sc = (float)sc;
     c.ecut = (float)ecut;
     c.sig2 = (float)c.sig2_d;
     c.eps4 = (float)c.eps4_d;
-    c.eps24 = (float)c.eps24_d;
+    c.neps24 = (float)(-c.eps24_d);
     c.ljshift = (float)ljs;
     c.L = (float)s->L;
     c.invL = (float)(1.0 / s->L);
-    c.ke = (float)COULOMB;
     c.qO_ke = (float)(COULOMB * f.q_O);
     c.qH_ke = (float)(COULOMB * (-0.5 * f.q_O));
-    c.p_alpha = (float)(0.3275911 * a);
-    c.neg_a2_log2e = (float)(-a * a * 1.4426950408889634);
+    c.tscale = (float)(2.0 / (rc * rc));
+    list_bucket_params(s, &c.bucket_lo, &c.bucket_inv);
+    const double half = 0.5 * rc * rc;   // s = (t + 1) rc^2 / 2
+    chebyshev_fit([&](double t) { return dsf_G(a, (t + 1.0) * half); }, c.gpoly);
+    chebyshev_fit([&](double t) { return dsf_E(a, (t + 1.0) * half); }, c.epoly);
     return c;
 }
 
@@ -726,6 +929,7 @@ PairArgs make_pair_args(const qhp_system_s* s) {
     A.pos = s->pos_f4;
     A.start = s->nbr_start;
     A.count = s->nbr_count;
+    A.nO = s->nbr_nO;
     A.nbr = s->nbr;
     A.charge_s = s->charge_s;
     A.type_s = s->type_s;
@@ -733,6 +937,7 @@ PairArgs make_pair_args(const qhp_system_s* s) {
     A.F = s->Ffix;
     A.epair = s->e_pair;
     A.status = s->status;
+    A.dev_max = s->pair_skip ? s->dev_max : nullptr;
     A.c = make_pair_consts(s);
     return A;
 }

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(128) k_grad_pairs(int N, int Pk, const double*
     const int k0 = start[i], k1 = k0 + count[i];
     for (int k = k0 + lane; k < k1; k += 32) {
         const int ex = nbr[k].x;
-        const int j = ex & 0x7fffffff;
+        const int j = entry_partner(ex);
         const bool Oj = ex >= 0;   // bit 31 marks an H partner
         S dd[3];
         for (int d = 0; d < 3; ++d) {

@@ -27,7 +27,7 @@ extern "C" int qhp_get_list_row(qhp_sys s, int atom, int* partners, int cap, int
     if (n > 0) e = cudaMemcpy(ent.data(), s->nbr + k0, sizeof(int4) * n, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(perm.data(), s->perm, sizeof(int) * s->N, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "qhp_get_list_row copy");
-    for (int k = 0; k < n && k < cap; ++k) partners[k] = perm[ent[k].x & 0x7fffffff];
+    for (int k = 0; k < n && k < cap; ++k) partners[k] = perm[entry_partner(ent[k].x)];
     *count = n;
     return QHP_OK;
 }

@@ -203,12 +203,12 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
         }
     }
     __syncthreads();
+    // mixed: the pair kernel's bead-pair records (bead_word layout), one component per thread
+    if (MIXED && valid) reinterpret_cast<float*>(A.pos_f4)[bead_word(A.iperm[a], n, d, P)] = xr[t];
     if (valid && d == 0) {
         const int base = la * 3 * P;
         const float x0 = xr[base + n], x1 = xr[base + P + n], x2 = xr[base + 2 * P + n];
         dv = x0 * x0 + x1 * x1 + x2 * x2;
-        // mixed: one 16-byte (x, y, z, 0) record per (sorted atom, bead) for the pair kernel
-        if (MIXED) A.pos_f4[(size_t)A.iperm[a] * P + n] = make_float4(x0, x1, x2, 0.0f);
     }
     block_max_atomic(dv, A.dev_max);
 }
@@ -426,7 +426,8 @@ __global__ void __launch_bounds__(128) k_contract(int N, int P, int Pc, const do
             if (n < P) f0 = fmaf(Cf[b * P + n], (float)q[n], f0);
             x[d] = (float)(q[0] - anchor[a * 3 + d]) + (f0 + f1);
         }
-        pos_c[(size_t)iperm[a] * Pc + b] = make_float4(x[0], x[1], x[2], 0.0f);
+        float* pw = reinterpret_cast<float*>(pos_c);
+        for (int d = 0; d < 3; ++d) pw[bead_word(iperm[a], b, d, Pc)] = x[d];
         dv = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     }
     for (int o = 16; o > 0; o >>= 1) dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, o));

@@ -12,6 +12,7 @@
 // with each operation rounded on its own (explicit _rn intrinsics, no FMA).  An
 // FP32 prefilter on wrapped centroids decides the candidates that are more than
 // 1e-3 A away from r_list; the rest get the exact FP64 test above.
+#include <algorithm>
 #include <vector>
 
 #include "qhp_internal.cuh"
@@ -444,7 +445,111 @@ __global__ void k_list_all(const int* flag, int N, double L, double r2max, const
     }
 }
 
+// Row order for the pair kernel: every row's entries sorted by (partner type, |D|^2 bucket) -
+// list_bucket - stably, so that equal keys keep the fill order and the result is a function of
+// the row's set of partners alone; also counts each row's O partners.  One block per row, the
+// row staged in shared memory: a stable counting sort in which the four warps take contiguous
+// quarters of the row, count keys per quarter, and scatter their quarters in order.
+constexpr int LS_THREADS = 128;
+constexpr int LS_WARPS = LS_THREADS / 32;
+constexpr int LS_KEYS = 2 * LIST_BUCKETS;
+static_assert(LS_KEYS <= LS_THREADS, "one thread per key in the per-key passes");
+
+__device__ __forceinline__ int list_key(int4 e, float lo, float inv) {
+    return (e.x < 0 ? LIST_BUCKETS : 0) + list_bucket(__int_as_float(e.y), __int_as_float(e.z), __int_as_float(e.w), lo, inv);
+}
+
+__global__ void __launch_bounds__(LS_THREADS) k_list_sort(const int* flag, const int* start, const int* count,
+                                                          int4* nbr, int* nO, float lo, float inv) {
+    if (!*flag) return;
+    extern __shared__ int4 row[];
+    __shared__ int hist[LS_WARPS][LS_KEYS];   // key counts per quarter, then each quarter's first slot per key
+    __shared__ int base[LS_KEYS];             // key totals, then their exclusive prefix sums
+    const int i = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int n = count[i];
+    int4* g = nbr + start[i];
+    for (int k = t; k < n; k += LS_THREADS) row[k] = g[k];
+    for (int k = t; k < LS_WARPS * LS_KEYS; k += LS_THREADS) (&hist[0][0])[k] = 0;
+    __syncthreads();
+    const int q = (n + LS_WARPS - 1) / LS_WARPS;
+    const int k0 = min(n, w * q), k1 = min(n, k0 + q);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int k = kb + lane;
+        const int key = k < k1 ? list_key(row[k], lo, inv) : -1 - lane;   // idle lanes: distinct dummies
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        if (k < k1 && (same & lt) == 0u) hist[w][key] += __popc(same);     // one lane per key
+        __syncwarp();
+    }
+    __syncthreads();
+    if (t < LS_KEYS) {
+        int sum = 0;
+        for (int v = 0; v < LS_WARPS; ++v) sum += hist[v][t];
+        base[t] = sum;
+    }
+    __syncthreads();
+    if (w == 0) {   // exclusive prefix over the keys, KPL consecutive keys per lane
+        constexpr int KPL = (LS_KEYS + 31) / 32;
+        int v[KPL], x = 0;
+        for (int k = 0; k < KPL; ++k) {
+            const int key = lane * KPL + k;
+            v[k] = key < LS_KEYS ? base[key] : 0;
+            x += v[k];
+        }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        int run = x;   // inclusive prefix through this lane's keys
+        for (int k = KPL - 1; k >= 0; --k) {
+            run -= v[k];
+            const int key = lane * KPL + k;
+            if (key < LS_KEYS) base[key] = run;
+        }
+    }
+    __syncthreads();
+    if (t < LS_KEYS) {
+        int sum = base[t];
+        for (int v = 0; v < LS_WARPS; ++v) {
+            const int h = hist[v][t];
+            hist[v][t] = sum;
+            sum += h;
+        }
+    }
+    __syncthreads();
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int k = kb + lane;
+        const int4 e = k < k1 ? row[k] : make_int4(0, 0, 0, 0);
+        const int key = k < k1 ? list_key(e, lo, inv) : -1 - lane;
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        if (k < k1) {   // the partner word takes the entry's bucket in bits 26-30
+            const int4 out = make_int4((e.x & ~(31 << ENTRY_J_BITS)) | ((key % LIST_BUCKETS) << ENTRY_J_BITS), e.y, e.z, e.w);
+            g[hist[w][key] + __popc(same & lt)] = out;
+        }
+        __syncwarp();
+        if (k < k1 && (same & lt) == 0u) hist[w][key] += __popc(same);
+        __syncwarp();
+    }
+    if (t == 0) nO[i] = base[LIST_BUCKETS];
+}
+
 }  // namespace
+
+void list_bucket_params(const qhp_system_s* s, float* lo, float* inv) {
+    const double l = std::max(0.0, s->ff.rc - 1.0);
+    *lo = (float)(l * l);
+    *inv = (float)((double)LIST_BUCKETS / (s->r_list * s->r_list - l * l));
+}
+
+// The limit is a property of the kernel, shared by every system: it is raised once to the
+// longest row the sort handles, so that no system's set-up lowers it below another's rows.
+int list_sort_prepare(int row_cap) {
+    if (row_cap > LIST_SORT_MAX_ROW) return QHP_ERR_ARG;
+    QHP_CUDA(cudaFuncSetAttribute(k_list_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(int4) * (size_t)LIST_SORT_MAX_ROW)));
+    return QHP_OK;
+}
 
 cudaError_t launch_list_check(qhp_system_s* s, bool force) {
     const float half = (float)(0.5 * s->ff.skin);
@@ -501,7 +606,11 @@ cudaError_t launch_rebuild(qhp_system_s* s) {
         k_list_all<true><<<gW, wb, 0, st>>>(flag, N, s->L, r2max, s->mol_s, s->type_s, s->anchor, s->nbr_count, s->nbr_start,
                                             s->nbr, s->row_cap, s->status);
     }
-    s->launches += 2;
+    float blo, binv;
+    list_bucket_params(s, &blo, &binv);
+    k_list_sort<<<N, LS_THREADS, sizeof(int4) * (size_t)s->row_cap, st>>>(flag, s->nbr_start, s->nbr_count, s->nbr,
+                                                                          s->nbr_nO, blo, binv);
+    s->launches += 3;
     return cudaGetLastError();
 }
 

@@ -117,6 +117,47 @@ enum : int {
     MT_N = 8
 };
 
+// Mixed-precision bead positions (FP32 offsets from the atom's anchor), sorted atom order.
+// With P >= 2 each sorted atom owns a record of bead_stride(P) floats (a multiple of 16 bytes):
+// an xy plane of P/2 float4 {x_2k, x_2k+1, y_2k, y_2k+1}, then a z plane of P floats.  The pair
+// kernel, whose lanes carry two beads, then reads a partner's beads with one 16-byte and one
+// 8-byte load per lane over contiguous bytes (at P = 32 three 128-byte lines per partner,
+// against four for one float4 per bead).  P = 1 keeps one {x, y, z, -} record per atom.
+__host__ __device__ constexpr int bead_stride(int P) { return P == 1 ? 4 : (3 * P + 3) / 4 * 4; }
+// Float offset of component c of bead b of sorted atom s.
+__host__ __device__ __forceinline__ size_t bead_word(int s, int b, int c, int P) {
+    if (P == 1) return (size_t)s * 4 + c;
+    const size_t base = (size_t)s * bead_stride(P);
+    return c < 2 ? base + (size_t)(b >> 1) * 4 + 2 * c + (b & 1) : base + 2 * P + b;
+}
+
+// Order of the entries within a list row: partners that are O first (their pairs carry the
+// LJ term and one charge product), then H; within each group by bucket of the squared anchor
+// distance |D|^2: LIST_BUCKETS equal buckets of [lo, r_list^2) with lo = (rc - 1 A)^2, closer
+// entries in bucket 0.  The bucket is a monotone function of |D|^2 (each FP32 operation is), so
+// an entry in a bucket above bucket(R^2) lies farther than R: the pair kernel skips the tail of
+// a group that lies beyond reach, recomputing the same bucket from the same operations.
+constexpr int LIST_BUCKETS = 32;
+__device__ __forceinline__ int list_bucket_d2(float d2, float lo, float inv) {
+    const float b = __fmul_rn(__fsub_rn(d2, lo), inv);
+    return b < 1.0f ? 0 : (b < (float)(LIST_BUCKETS - 1) ? (int)b : LIST_BUCKETS - 1);
+}
+__device__ __forceinline__ int list_bucket(float Dx, float Dy, float Dz, float lo, float inv) {
+    return list_bucket_d2(__fadd_rn(__fadd_rn(__fmul_rn(Dx, Dx), __fmul_rn(Dy, Dy)), __fmul_rn(Dz, Dz)), lo, inv);
+}
+// List entry {partner word, D_x, D_y, D_z}: the partner word holds the partner's sorted index
+// in bits 0-25, its distance bucket in bits 26-30 (written by the row sort) and "partner is H"
+// in bit 31.
+constexpr int ENTRY_J_BITS = 26;
+constexpr int MAX_ATOMS = 1 << ENTRY_J_BITS;
+static_assert(LIST_BUCKETS <= 32, "the bucket fits the partner word's five bits");
+__host__ __device__ __forceinline__ int entry_partner(int x) { return x & (MAX_ATOMS - 1); }
+__host__ __device__ __forceinline__ int entry_bucket(int x) { return (x >> ENTRY_J_BITS) & 31; }
+__host__ __device__ __forceinline__ bool entry_is_h(int x) { return x < 0; }
+
+// Longest list row the in-place row sort handles (its shared-memory copy of the row).
+constexpr int LIST_SORT_MAX_ROW = 12288;
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -167,7 +208,7 @@ struct qhp_system_s {
     double *Q = nullptr, *Pm = nullptr, *fmode = nullptr;    // [N][3][P]
     double *Fd = nullptr;                                    // FP64 bead forces [N][3][P]
     long long* Ffix = nullptr;                               // mixed bead forces, fixed point [N][3][P]
-    float4* pos_f4 = nullptr;                                // mixed: sorted [N][P] (x, y, z, 0) - anchor
+    float4* pos_f4 = nullptr;                                // mixed: sorted, bead_word layout, offsets from anchor
     double* pos_d = nullptr;                                 // fp64: sorted [3][N][P], absolute
     double* anchor = nullptr;                                // [N][3] centroids at the last build
     float* dA = nullptr;                                     // mixed: [n_mol][2][4] min-image A_H - A_O
@@ -184,6 +225,7 @@ struct qhp_system_s {
     float4* cwl = nullptr;                                   // their low parts: wrapped = cw + cwl (double-float)
     int* nbr_start = nullptr;                                // [N+1], row i starts at i * row_cap
     int* nbr_count = nullptr;                                // [N] row lengths
+    int* nbr_nO = nullptr;                                   // [N] leading entries of a row whose partner is O
     int4* nbr = nullptr;                                     // entries {j, Dx, Dy, Dz}
     int64_t nbr_cap = 0;                                     // N * row_cap
     int row_cap = 0;                                         // entries per row
@@ -201,6 +243,7 @@ struct qhp_system_s {
     int64_t rebuilds_host = 0;
     int keep_anchor = 0;           // 1 while a checkpoint restore rebuilds from stored anchors
     int pair_w = 0;                // warps per atom of the mixed pair kernel (0: default for P)
+    int pair_skip = 1;             // 1: the mixed pair kernel skips list entries beyond reach
     // RESPA (Sec. III.A.2): n inner steps per outer step; slow (nonbonded) forces on pc
     // contracted beads; fast (bonded) forces in Ffix / fmode
     int respa_n = 0;               // 0: plain BAOAB
@@ -328,6 +371,8 @@ cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2);
 cudaError_t launch_gather_centroids(qhp_system_s* s, double* out);
 cudaError_t launch_step_counter(qhp_system_s* s);
 int host_list_size(qhp_system_s* s, int64_t* max_row);
+void list_bucket_params(const qhp_system_s* s, float* lo, float* inv);   // the row sort's bucket map
+int list_sort_prepare(int row_cap);             // shared-memory limit of the row sort for rows of row_cap
 int rebuild_list_now(qhp_system_s* s);   // synchronous; checks the beads are covered
 void graph_invalidate(qhp_system_s* s);  // drop the captured step graph (its parameters changed)
 int system_sync(qhp_system_s* s);        // synchronise the system's stream, report its status

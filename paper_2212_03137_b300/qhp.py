@@ -103,6 +103,7 @@ _SIGS = {
     "qhp_batch_get_profile": [_VP, _VP],
     "qhp_autotune": [_VP, C.c_int, _IP],
     "qhp_set_pair_warps": [_VP, C.c_int],
+    "qhp_set_pair_skip": [_VP, C.c_int],
     "qhp_state_energies": [_VP, _DP, _DP, _DP],
     "qhp_bar": [_DP, C.c_int, _DP, C.c_int, C.c_double, C.c_double, _DP, _IP],
     "qhp_energy_grad": [_VP, _DP, _DP, _DP],
@@ -423,6 +424,10 @@ def qhp_autotune(h, reps: int = 5) -> int:
 
 def qhp_set_pair_warps(h, w: int) -> None:
     _check(lib().qhp_set_pair_warps(h, int(w)))
+
+
+def qhp_set_pair_skip(h, enabled: bool) -> None:
+    _check(lib().qhp_set_pair_skip(h, 1 if enabled else 0))
 
 
 class Batch:

@@ -2,16 +2,18 @@
 
 The nonbonded sum of Sec. III.A.3 (one centroid list shared by all beads) is compiled
 per bead count and per warps-per-atom split:
-- P < 32: a warp takes 32/P entries at a time; with P = 2 and 4, four entries per lane
-  are in flight.
-- P = 16 and 32: the lanes are the beads.
-- P = 64: two beads per lane.
-- W = 1, 2 or 4 warps share one atom's row.
+- P >= 2: a lane carries two beads of one list entry (packed FP32x2 arithmetic), so a warp
+  takes 64/P entries at a time; P = 1: a lane takes one entry.
+- W = 1, 2 or 4 warps share one atom's row, by blocks of 32 entries.
 
 Each is compared with the oracle on sampled beads of a 343-water box (1,029 atoms, a
 multiple of no block's atom count). The small-box path (per-bead minimum image over a
 brute-force row) is compared on the 64-water box. The energy variant of the kernel is
 checked through the bead-averaged potential.
+
+The forces must not depend on W (every block of 32 entries is summed in FP32 and converted
+to int64 once, and the integers are added), nor on skipping the entries that lie beyond
+reach of every bead: both are checked bit for bit.
 """
 import dataclasses
 
@@ -51,9 +53,14 @@ def _check_all_splits(cfg, list_mode):
                 err = rms_rel(F[b], Fo[k])
                 assert err < 1e-5, (P, W, b, err)
             forces[W] = F
-        # the splits differ only in the FP32 summation order of each atom's row
+        # block sums are converted to integers before the splits combine them: same bits
         for W in (2, 4):
-            assert rms_rel(forces[W], forces[1]) < 1e-6, W
+            assert np.array_equal(forces[W], forces[1]), W
+        # entries beyond reach of every bead add exactly nothing: skipping them keeps the bits
+        qhp.qhp_set_pair_skip(s.h, False)
+        qhp.qhp_compute_forces(s.h)
+        assert np.array_equal(qhp.qhp_get_forces(s.h), forces[4])
+        qhp.qhp_set_pair_skip(s.h, True)
         qhp.qhp_set_pair_warps(s.h, 0)
         e = qhp.qhp_get_energy(s.h)
     if P <= 8:   # bead-averaged potential from every bead (Eq. (3))
