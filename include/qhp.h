@@ -91,7 +91,10 @@ typedef struct {
  * spring     = sum_{n>0} 1/2 m omega_n^2 Q_n^2                 (Eq. (1))
  * kinetic_nm = sum_n P_n^2 / 2m                               (Eq. (7))
  * kinetic_cv = 3N kT/2 - (1/2P) sum_i (x_i - Q_0).F(x_i)      (Eq. (6))
- * fdt_delta  = mean |Delta_bar_FDT| of the last segment, adQTB (Eq. (21)) */
+ * fdt_delta  = adQTB: mean of |Delta_bar_FDT,z(omega_j)| (Eq. (21), the type mean of
+ *              Sec. III.B.2, kcal/mol) over both atom types and the n_seg + 1 frequency bins
+ *              of the last completed segment, with the gamma that segment ran with; 0 before
+ *              the first segment end and without adQTB */
 typedef struct {
     double potential, spring, kinetic_nm, kinetic_cv, fdt_delta;
     double bonded, nonbonded, reserved;

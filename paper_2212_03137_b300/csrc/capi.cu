@@ -472,7 +472,15 @@ int compute_energy(qhp_system_s* s, qhp_energy* out) {
     out->spring = h[2];
     out->kinetic_nm = h[3];
     out->kinetic_cv = 1.5 * N * kT - h[4] / (2.0 * P);
-    out->fdt_delta = s->fdt_delta_last;
+    out->fdt_delta = 0.0;
+    if (s->qtb_delta && s->n_seg > 0) {   // mean |Delta_bar_FDT,z(w_j)| over both types and all bins
+        const size_t nb = 2 * (size_t)(s->n_seg + 1);
+        std::vector<double> d(nb);
+        QHP_CUDA(cudaMemcpy(d.data(), s->qtb_delta, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+        double sum = 0.0;
+        for (double v : d) sum += fabs(v);
+        out->fdt_delta = sum / (double)nb;
+    }
     return QHP_OK;
 }
 

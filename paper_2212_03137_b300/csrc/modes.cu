@@ -167,9 +167,8 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
                 pm = pnew;
             } else {                                                  // O with white noise
                 const uint4 x = philox_draw(A.seed, (uint32_t)idx, step, TAG_OSTEP);
-                if (MIXED) {   // FP32 normal: the kick amp * R is formed in FP32 (1e-7 relative)
-                    const float ampf = reinterpret_cast<const float*>(c + MT_AMPF)[0];
-                    pm = c[MT_C1] * pm + f32_to_f64(ampf * normal_f32(x, 0));
+                if (MIXED) {   // FP32 normal, widened once; the thermostat update itself is FP64
+                    pm = fma(c[MT_AMP], f32_to_f64(normal_f32(x, 0)), c[MT_C1] * pm);
                 } else {
                     pm = c[MT_C1] * pm + c[MT_AMP] * normal_f64(x, 0);
                 }
@@ -537,8 +536,6 @@ void mode_constants(qhp_system_s* s) {
             c[MT_C1] = m.c1[n];
             c[MT_AMP] = m.amp[n] * sqrt(mass);
             c[MT_INV2M] = 0.5 / mass;
-            const float ampf = (float)c[MT_AMP];
-            memcpy(&c[MT_AMPF], &ampf, sizeof ampf);
         }
     }
 }

@@ -113,7 +113,6 @@ enum : int {
     MT_C1 = 2,      // exp(-gamma_n dt)
     MT_AMP = 3,     // sqrt((1 - c1^2) m kT) (PILE) or sqrt((1 - c1^2) m) (adQTB), A^2/ps^2 units
     MT_INV2M = 4,   // 1 / (2 m)
-    MT_AMPF = 5,    // MT_AMP rounded to FP32, stored in the slot's first four bytes
     MT_N = 8
 };
 
@@ -290,7 +289,6 @@ struct qhp_system_s {
     float* Tproj_f = nullptr;
 
     double* est_part = nullptr;    // estimator partial sums [3][blocks]
-    double fdt_delta_last = 0.0;
 
     // ---- state bookkeeping
     int64_t kernels_per_step = 0;     // kernels of a captured step outside the rebuild conditional
