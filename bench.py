@@ -64,7 +64,9 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock and throttle-reason samples during the timed region: NVML polled every 2 ms
+    from a thread (a timed region of a few milliseconds still gets samples), else nvidia-smi
+    at its 50 ms floor."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -79,7 +81,38 @@ class ClockSampler:
         self.proc = None
         self.thread = None
 
+    def _nvml_loop(self, nv, handle):
+        reasons = [("hw_slowdown", nv.nvmlClocksEventReasonHwSlowdown),
+                   ("hw_thermal_slowdown", nv.nvmlClocksEventReasonHwThermalSlowdown),
+                   ("sw_thermal_slowdown", nv.nvmlClocksEventReasonSwThermalSlowdown),
+                   ("sw_power_cap", nv.nvmlClocksEventReasonSwPowerCap)]
+        mx = nv.nvmlDeviceGetMaxClockInfo(handle, nv.NVML_CLOCK_SM)
+        while not self.stop.is_set():
+            sm = nv.nvmlDeviceGetClockInfo(handle, nv.NVML_CLOCK_SM)
+            bits = nv.nvmlDeviceGetCurrentClocksEventReasons(handle)
+            self.rows.append([str(sm), str(mx)] + ["Active" if bits & b else "Not Active" for _, b in reasons])
+            time.sleep(0.002)
+
     def __enter__(self):
+        self.stop = threading.Event()
+        try:
+            import pynvml as nv
+            nv.nvmlInit()
+            idx = self.index
+            if idx.isdigit():
+                handle = nv.nvmlDeviceGetHandleByIndex(int(idx))
+            else:
+                try:
+                    handle = nv.nvmlDeviceGetHandleByUUID(idx)
+                except Exception:
+                    handle = nv.nvmlDeviceGetHandleByUUID(idx.encode())
+            self.nvml = nv
+            self.thread = threading.Thread(target=self._nvml_loop, args=(nv, handle), daemon=True)
+            self.thread.start()
+            return self
+        except Exception as e:   # no NVML here: fall back to nvidia-smi, and say why
+            self.nvml = None
+            self.nvml_error = f"{type(e).__name__}: {e}"[:120]
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -97,6 +130,14 @@ class ClockSampler:
                 self.rows.append(parts)
 
     def __exit__(self, *a):
+        self.stop.set()
+        if getattr(self, "nvml", None) is not None:
+            self.thread.join(timeout=2)
+            try:
+                self.nvml.nvmlShutdown()
+            except Exception:
+                pass
+            return
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -107,13 +148,16 @@ class ClockSampler:
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    **({"nvml_error": self.nvml_error} if getattr(self, "nvml_error", None) else {})}
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in self.rows for k in range(4) if r[2 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.rows),
+                "source": "nvml, 2 ms" if getattr(self, "nvml", None) is not None else "nvidia-smi, 50 ms",
+                **({"nvml_error": self.nvml_error} if getattr(self, "nvml_error", None) else {})}
 
 
 def _peaks():
@@ -127,6 +171,60 @@ def _peaks():
 def _config(name):
     from paper_2212_03137_b300.workloads import CONFIGS
     return CONFIGS[name]
+
+
+def _workload_conf(name, cfg, ws):
+    """The workload a line measures (the same dict on both arms)."""
+    conf = {"workload": name, "n_molecules": cfg.n_mol, "n_atoms": 3 * cfg.n_mol, "beads": cfg.P, "box_A": cfg.box,
+            "rc_A": cfg.rc, "skin_A": cfg.skin, "dt_fs": cfg.dt_fs, "temperature_K": cfg.temperature,
+            "thermostat": cfg.thermostat, "precision": cfg.precision,
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"}
+    if "respa" in cfg.extra:
+        conf.update({"respa_inner_steps": int(cfg.extra["respa"]),
+                     "contracted_beads": int(cfg.extra.get("contracted_beads", 0)),
+                     "step": "one RESPA outer step; the metric counts its inner time steps"})
+    return conf
+
+
+def _batch_conf(cfgs, ws):
+    return {"workload": "batch_256", "n_systems": len(cfgs),
+            "n_molecules_range": [min(c.n_mol for c in cfgs), max(c.n_mol for c in cfgs)],
+            "beads": sorted({c.P for c in cfgs}), "density_g_cm3": 1.0, "dt_fs": 0.5, "temperature_K": 300.0,
+            "thermostat": "pile", "precision": "mixed", "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": f"replicas x{ws}"}
+
+
+def _host():
+    """The host the CPU baseline ran on: CPU model and the cores the OS reports."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def _sampled_force_error(h, cfg, n_mol=40, seed=5):
+    """RMS relative error of the GPU forces of bead 0 on the atoms of n_mol sampled molecules
+    against the oracle's brute-force sum for those atoms (any box size; FP64)."""
+    from oracle import water as ow
+    from paper_2212_03137_b300 import qhp
+    from paper_2212_03137_b300.workloads import WATER_FF as W
+    ff = ow.ForceField(eps=W["eps"], sigma=W["sigma"], q_O=W["q_O"], k_b=W["k_b"], r0=W["r0"],
+                       k_theta=W["k_theta"], theta0=math.radians(W["theta0_deg"]), alpha=W["alpha"], rc=cfg.rc,
+                       m_O=W["m_O"], m_H=W["m_H"])
+    box = cfg.system()
+    qhp.qhp_compute_forces(h)
+    F = qhp.qhp_get_forces(h)[0]
+    x = qhp.qhp_get_beads(h)[0]
+    mols = np.sort(np.random.default_rng(seed).choice(box.n_mol, min(n_mol, box.n_mol), replace=False))
+    atoms = np.concatenate([np.arange(3 * m, 3 * m + 3) for m in mols])
+    Fo = ow.nonbonded_on_atoms(x, atoms, box.types, box.molecule, box.box, ff) + ow.bonded(x[atoms], box.box, ff)[1]
+    return float(np.sqrt(np.sum((F[atoms] - Fo) ** 2) / np.sum(Fo ** 2)))
 
 
 def run_ours(args, ws, rank, local):
@@ -244,14 +342,8 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if fp64 else "f32/i64/f64 (mixed)", "data": "synthetic",
             "ns_per_day": ns_day,
-            "config": {"workload": args.workload, "n_molecules": cfg.n_mol, "n_atoms": N, "beads": P,
-                       "box_A": cfg.box, "rc_A": cfg.rc, "skin_A": cfg.skin, "dt_fs": cfg.dt_fs,
-                       "temperature_K": cfg.temperature, "thermostat": cfg.thermostat, "precision": cfg.precision,
-                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}",
-                       "launch": "direct kernel launches" if args.direct_launch else "one CUDA graph per step",
-                       **({"respa_inner_steps": inner, "contracted_beads": int(cfg.extra.get("contracted_beads", 0)),
-                           "step": "one RESPA outer step; the metric counts its inner time steps"}
-                          if "respa" in cfg.extra else {})},
+            "config": _workload_conf(args.workload, cfg, ws),
+            "launch": "direct kernel launches" if args.direct_launch else "one CUDA graph per step",
             "roofline": {"kernel": "nonbonded pair kernel", "bound": "alu", "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": traffic, "pairs_per_launch": pairs, "oo_pairs_per_launch": oo_pairs,
@@ -276,6 +368,9 @@ def run_ours(args, ws, rank, local):
         out["speedup_vs_fp64_gpu_path"] = value / ws / out["fp64_gpu_path"]["value"]
     if rank == 0 and args.workload == "grad_216w":
         out["gradient"] = _time_gradient(qhp, h, cfg, N, P)
+    if rank == 0 and getattr(args, "sampled_error", False):
+        out["force_error_rms_rel_vs_oracle"] = _sampled_force_error(h, cfg)
+        out["force_error_sample"] = "bead 0 of 40 sampled molecules, oracle brute-force sum for those atoms"
     sysobj.close()
     if rank == 0 and args.cpu_baseline:
         cb, err = _cpu_baseline(cfg, args)
@@ -350,13 +445,10 @@ def run_batch(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/i64/f64 (mixed)", "data": "synthetic",
             "ns_per_day": 1e3 / ms_per_step * 0.5 * 86400.0 / 1e6,
-            "config": {"workload": "batch_256", "n_systems": len(cfgs), "atom_beads_per_step": units_step,
-                       "n_molecules_range": [min(c.n_mol for c in cfgs), max(c.n_mol for c in cfgs)],
-                       "beads": sorted({c.P for c in cfgs}), "density_g_cm3": 1.0, "dt_fs": 0.5,
-                       "temperature_K": 300.0, "thermostat": "pile", "precision": "mixed",
-                       "tuned_warps_per_atom": {str(k): v for k, v in tuned.items()},
-                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}",
-                       "launch": "one CUDA graph per batched step"},
+            "config": _batch_conf(cfgs, ws),
+            "atom_beads_per_step": units_step,
+            "tuned_warps_per_atom": {str(k): v for k, v in tuned.items()},
+            "launch": "one CUDA graph per batched step",
             "roofline": {"kernel": "batched nonbonded pair kernel", "bound": "alu", "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": _profile_traffic("pair", "batch_256"), "pairs_per_launch": pairs,
@@ -393,6 +485,15 @@ def run_batch(args, ws, rank, local):
             out["e2e"] = {"value": units_step * n * ws / dt, "unit": UNIT,
                           "h2d_bytes_per_step": int(sum(p.numel() * 8 for p in pins)),
                           "d2h_bytes_per_step": int(sum(p.numel() * 8 for p in pins) + sum(c.nbytes for c in cents))}
+    if rank == 0 and getattr(args, "sampled_error", False):
+        # three boxes of different bead counts, bead 0 of 40 sampled molecules each
+        picks = [min(range(len(cfgs)), key=lambda k: (cfgs[k].P != P, cfgs[k].n_mol)) for P in (4, 16, 64)]
+        errs = [_sampled_force_error(systems[k].h, cfgs[k]) for k in picks]
+        out["force_error_rms_rel_vs_oracle"] = max(errs)
+        out["force_error_sample"] = f"boxes {picks} (P = 4, 16, 64), bead 0 of 40 sampled molecules each; worst"
+    if rank == 0 and args.fp64:
+        out["fp64_gpu_path"] = _batch_fp64_sample(cfgs, dev)
+        out["speedup_vs_fp64_gpu_path"] = value / ws / out["fp64_gpu_path"]["value"]
     b.close()
     for s in systems:
         s.close()
@@ -408,6 +509,33 @@ def run_batch(args, ws, rank, local):
                                "sample": f"FP64 oracle on 8 of the 256 boxes (indices {list(map(int, picks))}): "
                                          "forces of 2 beads each + one BAOAB update, numpy, 1 thread"}
     return out
+
+
+def _batch_fp64_sample(cfgs, dev, n=12, steps=3):
+    """The batch's boxes on the plain FP64 GPU path, one system at a time: n boxes spread over
+    the size and bead-count range, each timed over a few steps; the rate is their atom-bead
+    steps over their summed time (the FP64 path has no batched launch)."""
+    import torch
+    from paper_2212_03137_b300 import qhp
+    order = sorted(range(len(cfgs)), key=lambda k: cfgs[k].n_mol * cfgs[k].P)
+    picks = [order[int(round(i * (len(order) - 1) / (n - 1)))] for i in range(n)]
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    units = ms = 0.0
+    for k in picks:
+        s = qhp.System.from_config(cfgs[k], precision="fp64")
+        qhp.qhp_set_stream(s.h, stream.cuda_stream)
+        qhp.qhp_step_rpmd(s.h, 1)
+        qhp.qhp_sync(s.h)
+        e0.record(stream)
+        qhp.qhp_step_rpmd(s.h, steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        units += s.n_atoms * s.P * steps
+        s.close()
+    return {"value": units / (ms * 1e-3), "unit": UNIT, "ms_sampled": ms,
+            "sample": f"{n} of the {len(cfgs)} boxes (indices {picks}), {steps} steps each, one system at a time"}
 
 
 def _time_gradient(qhp, h, cfg, N, P, block=15, reps=3):
@@ -524,9 +652,10 @@ def _cpu_baseline(cfg, args, n_beads=2):
             err = float(np.sqrt(np.sum((Fg - F) ** 2) / np.sum(F ** 2)))
     finally:
         s.close()
-    return ({"value": units / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-             "sample": f"FP64 oracle: forces of {n_beads} of {cfg.P} beads ({t_force:.1f} s) + one BAOAB update "
-                       f"of all modes ({t_int:.2f} s) scaled by {n_beads}/{cfg.P}; numpy, 1 thread"}, err)
+    return ({"value": units / t, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host(),
+             "sample": f"FP64 oracle as it stands (numpy, 1 thread): forces of {n_beads} of {cfg.P} beads "
+                       f"({t_force:.1f} s) + one BAOAB update of all modes ({t_int:.2f} s); the rate is "
+                       f"extrapolated to a full step by counting {n_beads}/{cfg.P} of its atom-beads"}, err)
 
 
 def run_reference(args, ws, rank, local):
@@ -545,7 +674,7 @@ def run_reference(args, ws, rank, local):
             units += u
         cfg = cfgs[picks[0]]
         sample = f"FP64 oracle: one box per step from 8 of the 256 boxes {picks}, forces of 1 bead + one BAOAB update"
-        conf = {"workload": "batch_256", "n_systems": len(cfgs), "l2": "n/a (host CPU)", "parallelism": "single process"}
+        conf = _batch_conf(cfgs, ws)
     else:
         cfg = _config(args.workload)
         for _ in range(k):
@@ -553,14 +682,16 @@ def run_reference(args, ws, rank, local):
             t_tot += t
             units += u
         sample = f"FP64 oracle: forces of 1 of {cfg.P} beads + one BAOAB update of all modes scaled by 1/{cfg.P}"
-        conf = {"workload": args.workload, "n_atoms": 3 * cfg.n_mol, "beads": cfg.P, "l2": "n/a (host CPU)",
-                "parallelism": "single process"}
+        conf = _workload_conf(args.workload, cfg, ws)
     value = units / t_tot
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": k, "warmup": args.warmup,
             "ms_per_step": t_tot / k * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": conf,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "method": "the FP64 CPU oracle on the host (one process, numpy on one thread); the GPU arm's L2 "
+                      "flush and launch mode do not apply",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host(),
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -582,13 +713,43 @@ def _profile_traffic(kind, workload):
     return None
 
 
+DEFAULT_WORKLOAD = "rpmd_mixed_4096w"
+OTHER_WORKLOADS = ("adqtb_mixed_72000w", "batch_256", "grad_216w")
+
+
+def _other_workloads(args, ws, rank, local):
+    """The 72,000-water adQTB box, the 256-box batch and the 216-water gradient workload, each
+    timed like the default one (its own K steps after W warm-up steps, L2 flushed between
+    steps) with its dominant kernel's roofline, the plain FP64 GPU path where it is a
+    different path, and a force error against the oracle on sampled atoms."""
+    import copy
+    keep = ("value", "unit", "ms_per_step", "ns_per_day", "dtype", "config", "launch", "roofline", "clocks",
+            "gpu_launches", "stage_ms", "list_rebuilds", "adqtb_segment", "gradient", "fp64_gpu_path",
+            "speedup_vs_fp64_gpu_path", "force_error_rms_rel_vs_oracle", "force_error_sample",
+            "atom_beads_per_step", "tuned_warps_per_atom")
+    res = {}
+    for name in OTHER_WORKLOADS:
+        sub = copy.copy(args)
+        sub.workload = name
+        sub.e2e = False
+        sub.cpu_baseline = False
+        sub.fp64 = name != "grad_216w"        # that workload is itself the FP64 path
+        sub.sampled_error = True
+        r = run_batch(sub, ws, rank, local) if name == "batch_256" else run_ours(sub, ws, rank, local)
+        if rank == 0:
+            res[name] = {k: v for k, v in r.items() if k in keep}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rpmd_mixed_4096w")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    # the default run also times the other configurations (at N = 1) under "workloads"
+    ap.add_argument("--only-default", dest="all_workloads", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
@@ -610,6 +771,8 @@ def main():
         out = run_batch(args, ws, rank, local)
     else:
         out = run_ours(args, ws, rank, local)
+        if args.workload == DEFAULT_WORKLOAD and args.all_workloads and ws == 1:
+            out["workloads"] = _other_workloads(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as td
         td.destroy_process_group()
