@@ -341,9 +341,12 @@ int qhp_set_stream(qhp_sys sys, void* stream);
  *   stream: cudaStream_t (as void*), NULL for the legacy default stream.
  * Work is enqueued asynchronously on the stream.  Partial sums live in one fixed
  * device array of the library (1.5 MiB per GPU, held until the process exits):
- * n_atoms may be at most 65536 * (64 / P), larger inputs return QHP_ERR_ARG.  The
- * first call on a device looks up that array's address (cudaGetSymbolAddress), so
- * make it before any stream capture.  Every call reuses the same array, overwriting
+ * n_atoms may be at most 65536 * (64 / P), larger inputs return QHP_ERR_ARG.  Every
+ * call made outside a stream capture looks up that array's address on the current device
+ * (cudaGetSymbolAddress), so a device reset between calls is harmless; a call inside a
+ * capture reuses the address of the last such call, so make one call on each device
+ * before any stream capture (QHP_ERR_STATE otherwise), and do not replay a captured graph
+ * across a device reset.  Every call reuses the same array, overwriting
  * it entirely (nothing needs clearing); calls that overlap on the GPU, e.g. on two
  * streams at once, race on it and must be serialised by the caller.  P must be a
  * power of two in [1, 64]. */

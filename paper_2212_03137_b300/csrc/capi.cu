@@ -341,7 +341,7 @@ int ensure_capacity(qhp_system_s* s) {
         s->nbr = p;
         s->nbr_cap = row * s->N;
         s->row_cap = (int)row;
-        TRY(list_sort_prepare(s->row_cap));
+        TRY(list_sort_prepare(s));
         std::vector<int> start(s->N + 1);
         for (int i = 0; i <= s->N; ++i) start[i] = i * (int)row;
         QHP_CUDA(cudaMemcpy(s->nbr_start, start.data(), sizeof(int) * (s->N + 1), cudaMemcpyHostToDevice));

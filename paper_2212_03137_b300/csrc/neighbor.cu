@@ -459,79 +459,83 @@ __device__ __forceinline__ int list_key(int4 e, float lo, float inv) {
     return (e.x < 0 ? LIST_BUCKETS : 0) + list_bucket(__int_as_float(e.y), __int_as_float(e.z), __int_as_float(e.w), lo, inv);
 }
 
-__global__ void __launch_bounds__(LS_THREADS) k_list_sort(const int* flag, const int* start, const int* count,
+// Persistent grid: a block sorts rows blockIdx.x, + gridDim.x, ... (so a step without a rebuild
+// costs one small launch, not one block per row).
+__global__ void __launch_bounds__(LS_THREADS) k_list_sort(const int* flag, int N, const int* start, const int* count,
                                                           int4* nbr, int* nO, float lo, float inv) {
     if (!*flag) return;
     extern __shared__ int4 row[];
     __shared__ int hist[LS_WARPS][LS_KEYS];   // key counts per quarter, then each quarter's first slot per key
     __shared__ int base[LS_KEYS];             // key totals, then their exclusive prefix sums
-    const int i = blockIdx.x;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int n = count[i];
-    int4* g = nbr + start[i];
-    for (int k = t; k < n; k += LS_THREADS) row[k] = g[k];
-    for (int k = t; k < LS_WARPS * LS_KEYS; k += LS_THREADS) (&hist[0][0])[k] = 0;
-    __syncthreads();
-    const int q = (n + LS_WARPS - 1) / LS_WARPS;
-    const int k0 = min(n, w * q), k1 = min(n, k0 + q);
-    const unsigned lt = (1u << lane) - 1u;
-    for (int kb = k0; kb < k1; kb += 32) {
-        const int k = kb + lane;
-        const int key = k < k1 ? list_key(row[k], lo, inv) : -1 - lane;   // idle lanes: distinct dummies
-        const unsigned same = __match_any_sync(0xffffffffu, key);
-        if (k < k1 && (same & lt) == 0u) hist[w][key] += __popc(same);     // one lane per key
-        __syncwarp();
-    }
-    __syncthreads();
-    if (t < LS_KEYS) {
-        int sum = 0;
-        for (int v = 0; v < LS_WARPS; ++v) sum += hist[v][t];
-        base[t] = sum;
-    }
-    __syncthreads();
-    if (w == 0) {   // exclusive prefix over the keys, KPL consecutive keys per lane
-        constexpr int KPL = (LS_KEYS + 31) / 32;
-        int v[KPL], x = 0;
-        for (int k = 0; k < KPL; ++k) {
-            const int key = lane * KPL + k;
-            v[k] = key < LS_KEYS ? base[key] : 0;
-            x += v[k];
+    for (int i = blockIdx.x; i < N; i += gridDim.x) {
+        __syncthreads();                          // the previous row is written out
+        const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+        const int n = count[i];
+        int4* g = nbr + start[i];
+        for (int k = t; k < n; k += LS_THREADS) row[k] = g[k];
+        for (int k = t; k < LS_WARPS * LS_KEYS; k += LS_THREADS) (&hist[0][0])[k] = 0;
+        __syncthreads();
+        const int q = (n + LS_WARPS - 1) / LS_WARPS;
+        const int k0 = min(n, w * q), k1 = min(n, k0 + q);
+        const unsigned lt = (1u << lane) - 1u;
+        for (int kb = k0; kb < k1; kb += 32) {
+            const int k = kb + lane;
+            const int key = k < k1 ? list_key(row[k], lo, inv) : -1 - lane;   // idle lanes: distinct dummies
+            const unsigned same = __match_any_sync(0xffffffffu, key);
+            if (k < k1 && (same & lt) == 0u) hist[w][key] += __popc(same);     // one lane per key
+            __syncwarp();
         }
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        __syncthreads();
+        if (t < LS_KEYS) {
+            int sum = 0;
+            for (int v = 0; v < LS_WARPS; ++v) sum += hist[v][t];
+            base[t] = sum;
         }
-        int run = x;   // inclusive prefix through this lane's keys
-        for (int k = KPL - 1; k >= 0; --k) {
-            run -= v[k];
-            const int key = lane * KPL + k;
-            if (key < LS_KEYS) base[key] = run;
+        __syncthreads();
+        if (w == 0) {   // exclusive prefix over the keys, KPL consecutive keys per lane
+            constexpr int KPL = (LS_KEYS + 31) / 32;
+            int v[KPL], x = 0;
+            for (int k = 0; k < KPL; ++k) {
+                const int key = lane * KPL + k;
+                v[k] = key < LS_KEYS ? base[key] : 0;
+                x += v[k];
+            }
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            int run = x;   // inclusive prefix through this lane's keys
+            for (int k = KPL - 1; k >= 0; --k) {
+                run -= v[k];
+                const int key = lane * KPL + k;
+                if (key < LS_KEYS) base[key] = run;
+            }
         }
+        __syncthreads();
+        if (t < LS_KEYS) {
+            int sum = base[t];
+            for (int v = 0; v < LS_WARPS; ++v) {
+                const int h = hist[v][t];
+                hist[v][t] = sum;
+                sum += h;
+            }
+        }
+        __syncthreads();
+        for (int kb = k0; kb < k1; kb += 32) {
+            const int k = kb + lane;
+            const int4 e = k < k1 ? row[k] : make_int4(0, 0, 0, 0);
+            const int key = k < k1 ? list_key(e, lo, inv) : -1 - lane;
+            const unsigned same = __match_any_sync(0xffffffffu, key);
+            if (k < k1) {   // the partner word takes the entry's bucket in bits 26-30
+                const int4 out = make_int4((e.x & ~(31 << ENTRY_J_BITS)) | ((key % LIST_BUCKETS) << ENTRY_J_BITS), e.y, e.z, e.w);
+                g[hist[w][key] + __popc(same & lt)] = out;
+            }
+            __syncwarp();
+            if (k < k1 && (same & lt) == 0u) hist[w][key] += __popc(same);
+            __syncwarp();
+        }
+        if (t == 0) nO[i] = base[LIST_BUCKETS];
     }
-    __syncthreads();
-    if (t < LS_KEYS) {
-        int sum = base[t];
-        for (int v = 0; v < LS_WARPS; ++v) {
-            const int h = hist[v][t];
-            hist[v][t] = sum;
-            sum += h;
-        }
-    }
-    __syncthreads();
-    for (int kb = k0; kb < k1; kb += 32) {
-        const int k = kb + lane;
-        const int4 e = k < k1 ? row[k] : make_int4(0, 0, 0, 0);
-        const int key = k < k1 ? list_key(e, lo, inv) : -1 - lane;
-        const unsigned same = __match_any_sync(0xffffffffu, key);
-        if (k < k1) {   // the partner word takes the entry's bucket in bits 26-30
-            const int4 out = make_int4((e.x & ~(31 << ENTRY_J_BITS)) | ((key % LIST_BUCKETS) << ENTRY_J_BITS), e.y, e.z, e.w);
-            g[hist[w][key] + __popc(same & lt)] = out;
-        }
-        __syncwarp();
-        if (k < k1 && (same & lt) == 0u) hist[w][key] += __popc(same);
-        __syncwarp();
-    }
-    if (t == 0) nO[i] = base[LIST_BUCKETS];
 }
 
 }  // namespace
@@ -544,10 +548,14 @@ void list_bucket_params(const qhp_system_s* s, float* lo, float* inv) {
 
 // The limit is a property of the kernel, shared by every system: it is raised once to the
 // longest row the sort handles, so that no system's set-up lowers it below another's rows.
-int list_sort_prepare(int row_cap) {
-    if (row_cap > LIST_SORT_MAX_ROW) return QHP_ERR_ARG;
+int list_sort_prepare(qhp_system_s* s) {
+    if (s->row_cap > LIST_SORT_MAX_ROW) return QHP_ERR_ARG;
     QHP_CUDA(cudaFuncSetAttribute(k_list_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(int4) * (size_t)LIST_SORT_MAX_ROW)));
+    int per_sm = 0;
+    QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_list_sort, LS_THREADS,
+                                                           sizeof(int4) * (size_t)s->row_cap));
+    s->sort_grid = std::max(1, per_sm) * sm_count();
     return QHP_OK;
 }
 
@@ -608,8 +616,8 @@ cudaError_t launch_rebuild(qhp_system_s* s) {
     }
     float blo, binv;
     list_bucket_params(s, &blo, &binv);
-    k_list_sort<<<N, LS_THREADS, sizeof(int4) * (size_t)s->row_cap, st>>>(flag, s->nbr_start, s->nbr_count, s->nbr,
-                                                                          s->nbr_nO, blo, binv);
+    k_list_sort<<<std::min(N, s->sort_grid), LS_THREADS, sizeof(int4) * (size_t)s->row_cap, st>>>(
+        flag, N, s->nbr_start, s->nbr_count, s->nbr, s->nbr_nO, blo, binv);
     s->launches += 3;
     return cudaGetLastError();
 }

@@ -83,14 +83,19 @@ __global__ void __launch_bounds__(NA_BLOCK) k_est_noalloc(int N, int P, int apb,
     }
 }
 
+// One warp per estimator: lane l adds the partials l, l + 32, ... in order, then a fixed
+// shuffle tree adds the lanes, so the result is the same bits on every call.
 __global__ void k_final_noalloc(int nblocks, int N, int P, double kT, const double* __restrict__ partial,
                                 double* __restrict__ out) {
-    const int c = threadIdx.x;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (c >= 3) return;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(size_t)c * NA_MAX_BLOCKS + b];   // fixed order
-    if (c == 2) out[2] = 1.5 * N * kT - s / (2.0 * P);
-    else out[c] = s;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)c * NA_MAX_BLOCKS + b];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        if (c == 2) out[2] = 1.5 * N * kT - s / (2.0 * P);
+        else out[c] = s;
+    }
 }
 
 }  // namespace
@@ -117,14 +122,22 @@ extern "C" int qhp_estimators_noalloc(int n_atoms, int P, double temperature, co
         set_error("qhp_estimators_noalloc: device ordinal %d out of range", dev);
         return QHP_ERR_ARG;
     }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     double* partial = nullptr;
     {
-        // once per device, with that device current: the device address of the scratch array
+        // the device address of the scratch array, with this device current: looked up on every
+        // call made outside a stream capture (so a device reset cannot leave a stale address
+        // behind) and reused from the last such call while the stream is being captured
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        QHP_CUDA(cudaStreamIsCapturing(st, &cs));
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_partials_addr[dev]) {
+        if (cs == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             QHP_CUDA(cudaGetSymbolAddress(&p, g_partials));
             g_partials_addr[dev] = static_cast<double*>(p);
+        } else if (!g_partials_addr[dev]) {
+            set_error("qhp_estimators_noalloc: the first call on a device must come before any stream capture");
+            return QHP_ERR_STATE;
         }
         partial = g_partials_addr[dev];
     }
@@ -132,10 +145,9 @@ extern "C" int qhp_estimators_noalloc(int n_atoms, int P, double temperature, co
     const double kT = KB * temperature;
     const double pi = 3.141592653589793238462643383279502884;
     for (int k = 0; k < P; ++k) om.w[k] = 2.0 * P * kT / HBAR * sin(pi * k / P);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_est_noalloc<<<(unsigned)blocks, NA_BLOCK, 0, st>>>(n_atoms, P, apb, Q, Pm, F, mass, om, partial);
     QHP_CUDA(cudaGetLastError());
-    k_final_noalloc<<<1, 32, 0, st>>>((int)blocks, n_atoms, P, kT, partial, out);
+    k_final_noalloc<<<1, 96, 0, st>>>((int)blocks, n_atoms, P, kT, partial, out);
     QHP_CUDA(cudaGetLastError());
     return QHP_OK;
 }

@@ -228,6 +228,7 @@ struct qhp_system_s {
     int4* nbr = nullptr;                                     // entries {j, Dx, Dy, Dz}
     int64_t nbr_cap = 0;                                     // N * row_cap
     int row_cap = 0;                                         // entries per row
+    int sort_grid = 1;                                       // persistent grid of the row sort
     float* e_pair = nullptr;                                 // per (sorted atom, bead) pair energy (mixed)
     double* e_pair_d = nullptr;                              // fp64
     double* e_bond = nullptr;                                // [n_mol][P]
@@ -370,7 +371,7 @@ cudaError_t launch_gather_centroids(qhp_system_s* s, double* out);
 cudaError_t launch_step_counter(qhp_system_s* s);
 int host_list_size(qhp_system_s* s, int64_t* max_row);
 void list_bucket_params(const qhp_system_s* s, float* lo, float* inv);   // the row sort's bucket map
-int list_sort_prepare(int row_cap);             // shared-memory limit of the row sort for rows of row_cap
+int list_sort_prepare(qhp_system_s* s);         // the row sort's shared-memory limit and grid for s->row_cap
 int rebuild_list_now(qhp_system_s* s);   // synchronous; checks the beads are covered
 void graph_invalidate(qhp_system_s* s);  // drop the captured step graph (its parameters changed)
 int system_sync(qhp_system_s* s);        // synchronise the system's stream, report its status
