@@ -40,6 +40,13 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 
 __device__ __forceinline__ int brev(int j, int logn) { return (int)(__brev((unsigned)j) >> (32 - logn)); }
 
+// Shared-memory layout of the FFT buffers: element e lives at e + e/16 (one spare float2 per
+// 16).  The strided passes touch elements 16a + b at once; the pad sends different a to
+// different banks, which also holds for the four-consecutive-element butterflies of the
+// shortest passes (threads 32 bytes apart), so no pass has bank conflicts.
+__host__ __device__ __forceinline__ int fpad(int e) { return e + (e >> 4); }
+__host__ __device__ __forceinline__ int fpad_len(int n) { return n + (n >> 4); }
+
 // The spectrum of a real signal pairs bin k with bin -k.  In bit-reversed storage (the
 // forward FFT's output) position p = brev(k) has its partner -k at the mirror of p
 // within p's power-of-two block [b, 2b): pm = 3b - 1 - p.  Item q in [0, n/2] visits each
@@ -72,15 +79,15 @@ __device__ void fft_dif_fwd(float2* const (&x)[NB], int n, int logn, const float
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 float2* X = x[u];
-                const float2 a0 = X[i0], a1 = X[i1], a2 = X[i2], a3 = X[i3];
+                const float2 a0 = X[fpad(i0)], a1 = X[fpad(i1)], a2 = X[fpad(i2)], a3 = X[fpad(i3)];
                 const float2 t0 = cadd(a0, a2), t2 = cmul(csub(a0, a2), wA);
                 const float2 t1 = cadd(a1, a3);
                 float2 t3 = cmul(csub(a1, a3), wA);
                 t3 = make_float2(t3.y, -t3.x);   // times W^{n/4} = -i
-                X[i0] = cadd(t0, t1);
-                X[i1] = cmul(csub(t0, t1), wB);
-                X[i2] = cadd(t2, t3);
-                X[i3] = cmul(csub(t2, t3), wB);
+                X[fpad(i0)] = cadd(t0, t1);
+                X[fpad(i1)] = cmul(csub(t0, t1), wB);
+                X[fpad(i2)] = cadd(t2, t3);
+                X[fpad(i3)] = cmul(csub(t2, t3), wB);
             }
         }
     }
@@ -90,9 +97,9 @@ __device__ void fft_dif_fwd(float2* const (&x)[NB], int n, int logn, const float
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 float2* X = x[u];
-                const float2 a = X[2 * g], b = X[2 * g + 1];
-                X[2 * g] = cadd(a, b);
-                X[2 * g + 1] = csub(a, b);
+                const float2 a = X[fpad(2 * g)], b = X[fpad(2 * g + 1)];
+                X[fpad(2 * g)] = cadd(a, b);
+                X[fpad(2 * g + 1)] = csub(a, b);
             }
         }
     }
@@ -106,9 +113,9 @@ __device__ void fft_dit_inv(float2* x, int n, int logn, const float2* __restrict
     if (logn & 1) {                         // odd number of stages: the first one alone
         __syncthreads();
         for (int g = threadIdx.x; g < (n >> 1); g += blockDim.x) {
-            const float2 a = x[2 * g], b = x[2 * g + 1];
-            x[2 * g] = cadd(a, b);
-            x[2 * g + 1] = csub(a, b);
+            const float2 a = x[fpad(2 * g)], b = x[fpad(2 * g + 1)];
+            x[fpad(2 * g)] = cadd(a, b);
+            x[fpad(2 * g + 1)] = csub(a, b);
         }
         h = 2;
         lh = 1;
@@ -120,16 +127,16 @@ __device__ void fft_dit_inv(float2* x, int n, int logn, const float2* __restrict
             const int q = g & (h - 1);
             const int i0 = ((g >> lh) << (lh + 2)) + q, i1 = i0 + h, i2 = i0 + 2 * h, i3 = i0 + 3 * h;
             const float2 w1 = cconj(__ldg(&tw[q * s])), w2 = cconj(__ldg(&tw[q * (s >> 1)]));
-            const float2 a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
+            const float2 a0 = x[fpad(i0)], a1 = x[fpad(i1)], a2 = x[fpad(i2)], a3 = x[fpad(i3)];
             const float2 b1 = cmul(a1, w1), b3 = cmul(a3, w1);
             const float2 u0 = cadd(a0, b1), u1 = csub(a0, b1), u2 = cadd(a2, b3), u3 = csub(a2, b3);
             const float2 c2 = cmul(u2, w2);
             float2 c3 = cmul(u3, w2);
             c3 = make_float2(-c3.y, c3.x);       // times W^{-n/4} = +i
-            x[i0] = cadd(u0, c2);
-            x[i2] = csub(u0, c2);
-            x[i1] = cadd(u1, c3);
-            x[i3] = csub(u1, c3);
+            x[fpad(i0)] = cadd(u0, c2);
+            x[fpad(i2)] = csub(u0, c2);
+            x[fpad(i1)] = cadd(u1, c3);
+            x[fpad(i3)] = csub(u1, c3);
         }
     }
     __syncthreads();
@@ -143,6 +150,7 @@ __device__ __forceinline__ float2 white_pair(uint64_t seed, uint32_t dof, uint64
 
 constexpr int GEN_PAIRS = 4;     // dof pairs per block -> 8 dofs = 32-byte output rows
 constexpr int GEN_THREADS = 512;
+constexpr int GEN_ROW = 9;       // floats per staged output row (8 dofs + 1 pad)
 
 // One colored-noise segment k for all dofs.
 __global__ void __launch_bounds__(GEN_THREADS) k_qtb_generate(int n_dof, int N, int log4n, int64_t seg,
@@ -151,8 +159,8 @@ __global__ void __launch_bounds__(GEN_THREADS) k_qtb_generate(int n_dof, int N, 
                                                               const float2* __restrict__ tw4, float* __restrict__ u) {
     extern __shared__ float2 sm[];
     const int n = 4 * N;
-    float2* buf = sm;                                  // [4N]
-    float* stage = reinterpret_cast<float*>(sm + n);   // [N][8]
+    float2* buf = sm;                                  // [fpad_len(4N)]
+    float* stage = reinterpret_cast<float*>(sm + fpad_len(n));   // [N][GEN_ROW]: 8 outputs, 1 pad
     float2* const bufs[1] = {buf};
     const int pair0 = blockIdx.x * GEN_PAIRS;
     for (int pp = 0; pp < GEN_PAIRS; ++pp) {
@@ -167,8 +175,8 @@ __global__ void __launch_bounds__(GEN_THREADS) k_qtb_generate(int n_dof, int N, 
                 if (va) xa = white_pair(seed, (uint32_t)da, gs);
                 if (vb) xb = white_pair(seed, (uint32_t)db, gs);
             }
-            buf[t] = make_float2(xa.x, xb.x);
-            buf[t + 1] = make_float2(xa.y, xb.y);
+            buf[fpad(t)] = make_float2(xa.x, xb.x);
+            buf[fpad(t + 1)] = make_float2(xa.y, xb.y);
         }
         fft_dif_fwd<1>(bufs, n, log4n, tw4);   // bin k now sits at position brev(k)
         const int za = va ? dof_type[da] : 0, zb = vb ? dof_type[db] : 0;
@@ -177,35 +185,35 @@ __global__ void __launch_bounds__(GEN_THREADS) k_qtb_generate(int n_dof, int N, 
         for (int q = threadIdx.x; q <= n / 2; q += blockDim.x) {
             int pk, pm;
             pair_positions(q, pk, pm);
-            const float2 Xk = buf[pk], Xm = buf[pm];
+            const float2 Xk = buf[fpad(pk)], Xm = buf[fpad(pm)];
             const float2 Ak = make_float2(0.5f * (Xk.x + Xm.x), 0.5f * (Xk.y - Xm.y));   // (X_k + X*_-k)/2
             const float2 Bk = make_float2(0.5f * (Xk.y + Xm.y), -0.5f * (Xk.x - Xm.x));  // (X_k - X*_-k)/(2i)
             const float2 Yk = cadd(cmul(Ha[pk], Ak), cmul(make_float2(0.f, 1.f), cmul(Hb[pk], Bk)));
             if (pm != pk) {
                 const float2 Am = cconj(Ak), Bm = cconj(Bk);                                 // spectra of real signals
                 const float2 Ym = cadd(cmul(Ha[pm], Am), cmul(make_float2(0.f, 1.f), cmul(Hb[pm], Bm)));
-                buf[pm] = Ym;
+                buf[fpad(pm)] = Ym;
             }
-            buf[pk] = Yk;
+            buf[fpad(pk)] = Yk;
         }
         fft_dit_inv(buf, n, log4n, tw4);
         const float inv = 1.0f / (float)n;
         for (int m = threadIdx.x; m < N; m += blockDim.x) {
-            const float2 y = buf[N + m];
-            stage[m * 8 + 2 * pp] = y.x * inv;
-            stage[m * 8 + 2 * pp + 1] = y.y * inv;
+            const float2 y = buf[fpad(N + m)];
+            stage[m * GEN_ROW + 2 * pp] = y.x * inv;   // rows of 9 floats: consecutive m in distinct banks
+            stage[m * GEN_ROW + 2 * pp + 1] = y.y * inv;
         }
         __syncthreads();
     }
-    // coalesced write of the staged [N][8] block
+    // coalesced write of the staged block, 8 dofs per output row
     const int d0 = pair0 * 2;
     for (int e = threadIdx.x; e < N * 8; e += blockDim.x) {
         const int m = e >> 3, c = e & 7;
-        if (d0 + c < n_dof) u[(size_t)m * n_dof + d0 + c] = stage[e];
+        if (d0 + c < n_dof) u[(size_t)m * n_dof + d0 + c] = stage[m * GEN_ROW + c];
     }
 }
 
-constexpr int SPEC_THREADS = 256;
+constexpr int SPEC_THREADS = 512;   // with 1,025 bins (n_seg 1024): three per thread, 32 warps per SM
 constexpr int SPEC_DOFS = 4;   // dofs per tile: 16-byte row segments of v and F
 
 // acc[z] += a, acc[2 + z] += b with constant indices (registers, not memory)
@@ -221,7 +229,7 @@ __device__ __forceinline__ void add_typed(float* acc, int z, float a, float b) {
 
 // Per-block sums over dofs of |v~_k|^2 and Re(v~_k F~_k*) per type and bin (Eq. (22) without
 // its dt/N factor; the per-type FDT deviation is linear in them and is formed from the
-// sums in k_qtb_adapt).  Each thread owns the bins k = t, t + 256, ... (at most BPT): a
+// sums in k_qtb_adapt).  Each thread owns the bins k = t, t + 512, ... (at most BPT): a
 // tile of 4 dofs is summed in FP32, then added to FP64 running sums.  The block walks
 // tiles of 4 dofs, read as [step][4] rows.
 template <int BPT>
@@ -232,10 +240,13 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_qtb_spectra(int n_dof, int N, 
                                                               double* __restrict__ part) {
     extern __shared__ float2 sm[];
     const int n = 2 * N, nb = N + 1;
-    float2* bv = sm;                                         // [2N]
-    float2* bf = sm + n;                                     // [2N]
-    float* tv = reinterpret_cast<float*>(sm + 2 * n);        // [N][4]
-    float* tf = tv + N * SPEC_DOFS;                          // [N][4]
+    float2* bv = sm;                                         // [fpad_len(2N)]
+    float2* bf = sm + fpad_len(n);                           // [fpad_len(2N)]
+    // tiles of SPEC_DOFS dofs, one row of N + 8 floats per dof (the pad puts the 4 rows of a
+    // 32-element store in distinct banks; rows are read along the steps, contiguously)
+    const int row = N + 8;
+    float* tv = reinterpret_cast<float*>(sm + 2 * fpad_len(n));   // [SPEC_DOFS][N + 8]
+    float* tf = tv + SPEC_DOFS * row;                            // [SPEC_DOFS][N + 8]
     float2* const bufs[2] = {bv, bf};
     double acc[BPT][4];
 #pragma unroll
@@ -249,8 +260,8 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_qtb_spectra(int n_dof, int N, 
         for (int e = threadIdx.x; e < N * SPEC_DOFS; e += blockDim.x) {
             const int m = e / SPEC_DOFS, c = e % SPEC_DOFS;
             const bool ok = d0 + c < n_dof;
-            tv[e] = ok ? v[(size_t)m * n_dof + d0 + c] : 0.0f;
-            tf[e] = ok ? F[(size_t)m * n_dof + d0 + c] : 0.0f;
+            tv[c * row + m] = ok ? v[(size_t)m * n_dof + d0 + c] : 0.0f;
+            tf[c * row + m] = ok ? F[(size_t)m * n_dof + d0 + c] : 0.0f;
         }
         float ts[BPT][4];
 #pragma unroll
@@ -265,11 +276,11 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_qtb_spectra(int n_dof, int N, 
             for (int t = threadIdx.x; t < n; t += blockDim.x) {
                 float2 xv = make_float2(0.f, 0.f), xf = make_float2(0.f, 0.f);
                 if (t < N) {
-                    xv = make_float2(tv[t * SPEC_DOFS + 2 * pp], tv[t * SPEC_DOFS + 2 * pp + 1]);
-                    xf = make_float2(tf[t * SPEC_DOFS + 2 * pp], tf[t * SPEC_DOFS + 2 * pp + 1]);
+                    xv = make_float2(tv[(2 * pp) * row + t], tv[(2 * pp + 1) * row + t]);
+                    xf = make_float2(tf[(2 * pp) * row + t], tf[(2 * pp + 1) * row + t]);
                 }
-                bv[t] = xv;
-                bf[t] = xf;
+                bv[fpad(t)] = xv;
+                bf[fpad(t)] = xf;
             }
             fft_dif_fwd<2>(bufs, n, log2n, tw2);   // bin k at position brev(k)
             const int za = dof_type[da], zb = vb ? dof_type[db] : 0;
@@ -279,7 +290,7 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_qtb_spectra(int n_dof, int N, 
                 if (q >= nb) break;
                 int pk, pm;
                 pair_positions(q, pk, pm);
-                const float2 Xk = bv[pk], Xm = bv[pm], Yk = bf[pk], Ym = bf[pm];
+                const float2 Xk = bv[fpad(pk)], Xm = bv[fpad(pm)], Yk = bf[fpad(pk)], Ym = bf[fpad(pm)];
                 // spectra of the a and b signals at bin k (twice their values: the 1/2 of
                 // the real-pair split is applied squared, as 1/4, below)
                 const float var = Xk.x + Xm.x, vai = Xk.y - Xm.y, vbr = Xk.y + Xm.y, vbi = Xm.x - Xk.x;
@@ -436,14 +447,14 @@ int qalloc(qhp_system_s* s, T** p, size_t count) {
     return QHP_OK;
 }
 
-size_t gen_smem(int N) { return sizeof(float2) * 4 * N + sizeof(float) * 8 * N; }
-size_t spec_smem(int N) { return sizeof(float2) * 4 * N + sizeof(float) * 2 * SPEC_DOFS * N; }
+size_t gen_smem(int N) { return sizeof(float2) * fpad_len(4 * N) + sizeof(float) * GEN_ROW * N; }
+size_t spec_smem(int N) { return sizeof(float2) * 2 * fpad_len(2 * N) + sizeof(float) * 2 * SPEC_DOFS * (N + 8); }
 constexpr int SPEC_BLOCKS = 592;
 
-// bins per thread of the spectra kernel for N (n_seg <= 2048): ceil((N + 1) / 256)
+// bins per thread of the spectra kernel for N (n_seg <= 2048): ceil((N + 1) / 512)
 int spec_bpt(int N) {
     const int b = (N + 1 + SPEC_THREADS - 1) / SPEC_THREADS;
-    return b <= 1 ? 1 : b <= 2 ? 2 : b <= 3 ? 3 : b <= 5 ? 5 : 9;
+    return b <= 1 ? 1 : b <= 2 ? 2 : b <= 3 ? 3 : 5;
 }
 
 template <int B>
@@ -454,8 +465,7 @@ const void* spectra_kernel_for(int N) {
         case 1: return spectra_kernel<1>();
         case 2: return spectra_kernel<2>();
         case 3: return spectra_kernel<3>();
-        case 5: return spectra_kernel<5>();
-        default: return spectra_kernel<9>();
+        default: return spectra_kernel<5>();
     }
 }
 
@@ -481,8 +491,7 @@ cudaError_t launch_spectra(qhp_system_s* s, int blocks) {
         case 1: QHP_SPEC(1); break;
         case 2: QHP_SPEC(2); break;
         case 3: QHP_SPEC(3); break;
-        case 5: QHP_SPEC(5); break;
-        default: QHP_SPEC(9); break;
+        default: QHP_SPEC(5); break;
     }
 #undef QHP_SPEC
     return cudaGetLastError();
@@ -561,7 +570,6 @@ int qtb_setup(qhp_system_s* s) {
         QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
         QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
         QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
-        QHP_CUDA(cudaFuncSetAttribute(k_qtb_spectra<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(2048)));
     }
     std::vector<double> g(2 * (size_t)(N + 1), s->th.gamma0);
     QHP_CUDA(cudaMemcpy(s->qtb_gamma, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice));

@@ -5,8 +5,8 @@ per-type FDT deviation (Eq. (21), averaged over the type's dofs, Sec. III.B.2), 
 (SIMPLE, Eq. (23), or RATIO, Eqs. (24)-(26)) and generates the next colored-noise segment
 (Sec. III.B.1).  Here the oracle recomputes each of those from the GPU's own records of the
 segment, which isolates the end-of-segment kernels from the trajectory:
-- the spectra kernel is specialised on n_seg (bins per thread 2, 5 and 9 for n_seg = 256,
-  1024 and 2048), so each of those runs once on a 64-water box;
+- the spectra kernel is specialised on n_seg (bins per thread 1, 2, 3 and 5 for n_seg = 256,
+  512, 1024 and 2048), so each of those runs once on a 64-water box;
 - the 8,000-water box runs the config-3 segment length (1024) with all 72,000 dofs averaged.
 
 Tolerances: the records and FFTs are FP32 (~1e-6 relative after an FFT of a few thousand
@@ -113,7 +113,7 @@ def _segment_end(cfg, adapt, n_sample_dofs=24):
     np.testing.assert_allclose(u1[:, dofs], u_want, rtol=0, atol=1e-3 * rms)
 
 
-@pytest.mark.parametrize("n_seg", [256, 1024, 2048])
+@pytest.mark.parametrize("n_seg", [256, 512, 1024, 2048])
 @pytest.mark.parametrize("adapt", ["simple", "ratio"])
 def test_segment_end_every_spectra_specialisation(n_seg, adapt):
     _segment_end(_cfg(64, 12.42, n_seg), adapt)
