@@ -41,7 +41,9 @@ enum {
     QHP_ERR_NONFINITE = -4,     /* NaN/Inf found in the state */
     QHP_ERR_LIST_OVERFLOW = -5, /* neighbour list larger than its buffer */
     QHP_ERR_STATE = -6,         /* call out of order (e.g. step before set_beads) */
-    QHP_ERR_NOMEM = -7          /* device allocation failed */
+    QHP_ERR_NOMEM = -7,         /* device allocation failed */
+    QHP_ERR_BOUNDS = -8         /* an index read from device data was out of range (bounds-checked
+                                   builds only, built with -DQHP_CHECK; plain builds never check) */
 };
 
 enum { QHP_FP64 = 0, QHP_MIXED = 1 };

@@ -12,6 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqhp.so")
+LIB_CHECK = os.path.join(HERE, "libqhp_check.so")
 SOURCES = ["capi.cu", "modes.cu", "neighbor.cu", "forces.cu", "qtb.cu", "noalloc.cu", "inspect.cu", "grad.cu", "batch.cu", "bar.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -23,20 +24,24 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
+def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None, check: bool = False) -> str:
     """Compile every source to an object in parallel (each is a self-contained translation
-    unit: no device code crosses files), then link the shared library."""
+    unit: no device code crosses files), then link the shared library.  check = True builds
+    the bounds-checked variant libqhp_check.so (-DQHP_CHECK: indices read from device data
+    are tested before use and reported as QHP_ERR_BOUNDS)."""
     from concurrent.futures import ThreadPoolExecutor
 
+    lib = LIB_CHECK if check else LIB
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, "qhp_internal.cuh"), os.path.join(HERE, "..", "include", "qhp.h")]
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= t for d in deps):
-            return LIB
-    objdir = os.path.join(HERE, "_build")
+            return lib
+    objdir = os.path.join(HERE, "_build_check" if check else "_build")
     os.makedirs(objdir, exist_ok=True)
-    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", *(extra or [])]
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", *(["-DQHP_CHECK"] if check else []),
+             *(extra or [])]
     if verbose:
         flags.insert(0, "-Xptxas=-v")
 
@@ -55,12 +60,12 @@ def build(verbose: bool = False, force: bool = False, extra: list[str] | None = 
         if res.returncode != 0:
             sys.stderr.write(res.stdout + res.stderr)
             raise RuntimeError(f"nvcc failed compiling {os.path.basename(obj)}")
-    link = [nvcc(), *ARCH, "-shared", "-o", LIB, *(o for o, _, _ in results), "-lcudart"]
+    link = [nvcc(), *ARCH, "-shared", "-o", lib, *(o for o, _, _ in results), "-lcudart"]
     res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed linking libqhp.so")
-    return LIB
+        raise RuntimeError(f"nvcc failed linking {os.path.basename(lib)}")
+    return lib
 
 
 if __name__ == "__main__":

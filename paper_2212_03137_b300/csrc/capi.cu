@@ -100,6 +100,10 @@ int check_status(qhp_system_s* s, unsigned st) {
         qhp::set_error("device wait timed out");
         return QHP_ERR_TIMEOUT;
     }
+    if (st & ST_BOUNDS) {
+        qhp::set_error("an index read from device data was out of range (bounds-checked build); the access was skipped");
+        return QHP_ERR_BOUNDS;
+    }
     return QHP_OK;
 }
 

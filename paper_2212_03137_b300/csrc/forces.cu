@@ -317,6 +317,8 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
                 }
                 const unsigned am0 = __ballot_sync(0xffffffffu, a0);
                 const unsigned am1 = __ballot_sync(0xffffffffu, a1);
+                if (a0) a0 = QHP_IN_BOUNDS(entry_j(e0.x), A.N, A.status);
+                if (a1) a1 = QHP_IN_BOUNDS(entry_j(e1.x), A.N, A.status);
                 if (am0 == 0u) {
                     beyond = true;
                     break;
@@ -361,12 +363,15 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
                     break;
                 }
                 const int nit = (__popc(am) + EPI - 1) / EPI;   // active entries form a prefix (bucket order)
-                const float dx = lane < n ? __int_as_float(e.y) : 0.5f * c.L;
-                const float dy = lane < n ? __int_as_float(e.z) : 0.5f * c.L;
-                const float dz = lane < n ? __int_as_float(e.w) : 0.5f * c.L;
+                float dx = 0.5f * c.L, dy = 0.5f * c.L, dz = 0.5f * c.L;
+                int jj = L.i;
+                if (lane < n && QHP_IN_BOUNDS(entry_j(e.x), A.N, A.status)) {
+                    dx = __int_as_float(e.y), dy = __int_as_float(e.z), dz = __int_as_float(e.w);
+                    jj = entry_j(e.x);
+                }
                 __syncwarp();
                 ent[lane][0] = make_float4(dx, dx, dy, dy);
-                ent[lane][1] = make_float4(dz, dz, __int_as_float(lane < n ? entry_j(e.x) : L.i), 0.0f);
+                ent[lane][1] = make_float4(dz, dz, __int_as_float(jj), 0.0f);
                 __syncwarp();
                 for (int it = 0; it < nit; ++it) {
                     const float4 a = ent[it * EPI + L.slot][0], b = ent[it * EPI + L.slot][1];
@@ -427,7 +432,8 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& s
         }
     }
     const int ka = A.start[i];
-    const int cnt = ok ? A.count[i] : 0;
+    int cnt = ok ? A.count[i] : 0;
+    if (!QHP_IN_BOUNDS(cnt, A.start[i + 1] - ka + 1, A.status)) cnt = 0;   // a row never passes its slot
     const int nO = ok ? min(A.nO[i], cnt) : 0;
     float2 en = f2(0.0f);
     // O partners: blocks wa, wa + W, ... of the group; H partners: numbered after the O blocks
@@ -535,6 +541,7 @@ __global__ void __launch_bounds__(128) k_pair_fp64_rows(int N, int P, const doub
     for (int k = k0 + lane; k < k1; k += 32) {
         const int ex = __ldg(&nbr[k].x);
         const int j = entry_j(ex);
+        if (!QHP_IN_BOUNDS(j, N, status)) continue;
         const bool Oj = !entry_is_h(ex);
         const double qq = qi * (Oj ? q_O : q_H);
         double dx = pos[((size_t)0 * N + j) * P + b] - xi;
@@ -615,6 +622,7 @@ __global__ void __launch_bounds__(128) k_pair_fp64_beads(int N, int P, const dou
         for (int k = k0 + jsub; k < k1; k += JPW) {
             const int ex = __ldg(&nbr[k].x);
             const int j = entry_j(ex);
+            if (!QHP_IN_BOUNDS(j, N, status)) continue;
             const bool Oj = !entry_is_h(ex);
             const double qq = qi * (Oj ? q_O : q_H);
             double dx = pos[((size_t)0 * N + j) * P + b] - xi;
@@ -678,6 +686,7 @@ struct BondArgs {
     double* ebond;
     BondConsts c;
     int overwrite;   // mixed: store the bonded forces instead of adding them to the pair forces
+    const unsigned* status;
 };
 
 template <bool MIXED, bool ENERGY>
@@ -695,6 +704,7 @@ __device__ __forceinline__ void bonded_body(const BondArgs& A, int t) {
     const int m = t / P, b = t % P;
     const int aO = 3 * m, aH1 = aO + 1, aH2 = aO + 2;
     const int sO = iperm[aO], s1 = iperm[aH1], s2 = iperm[aH2];
+    if (!(QHP_IN_BOUNDS(sO, N, A.status) && QHP_IN_BOUNDS(s1, N, A.status) && QHP_IN_BOUNDS(s2, N, A.status))) return;
     if (MIXED) {
         float d1[3], d2[3];
         const float* pw = reinterpret_cast<const float*>(pos_f);
@@ -975,6 +985,7 @@ BondArgs make_bond_args(const qhp_system_s* s) {
     B.ebond = s->e_bond;
     B.c = BondConsts{s->ff.k_b, s->ff.r0, s->ff.k_theta, s->ff.theta0, s->L};
     B.overwrite = 0;
+    B.status = s->status;
     return B;
 }
 

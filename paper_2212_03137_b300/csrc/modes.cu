@@ -39,6 +39,7 @@ struct IntegrateArgs {
     const int* gate;       // if set, the kernel runs only when *gate != 0
     const double* fmode_s; // RESPA: slow mode forces kicked together with the fast ones
     double ws;             //        with weight ws (n_alt on the first inner step, else 0)
+    const unsigned* status;
 };
 
 __device__ __forceinline__ void block_max_atomic(float v, unsigned* out) {
@@ -197,13 +198,14 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
         } else {
             double acc = 0.0;
             acc = dot4(Tsd + n, P, qs + base, 0, P);
-            A.pos_d[((size_t)d * A.N + A.iperm[a]) * P + n] = acc;
+            if (QHP_IN_BOUNDS(A.iperm[a], A.N, A.status)) A.pos_d[((size_t)d * A.N + A.iperm[a]) * P + n] = acc;
             xr[t] = f64_to_f32(acc - A.anchor[a * 3 + d]);
         }
     }
     __syncthreads();
     // mixed: the pair kernel's bead-pair records (bead_word layout), one component per thread
-    if (MIXED && valid) reinterpret_cast<float*>(A.pos_f4)[bead_word(A.iperm[a], n, d, P)] = xr[t];
+    if (MIXED && valid && QHP_IN_BOUNDS(A.iperm[a], A.N, A.status))
+        reinterpret_cast<float*>(A.pos_f4)[bead_word(A.iperm[a], n, d, P)] = xr[t];
     if (valid && d == 0) {
         const int base = la * 3 * P;
         const float x0 = xr[base + n], x1 = xr[base + P + n], x2 = xr[base + 2 * P + n];
@@ -571,6 +573,7 @@ static IntegrateArgs make_iargs(qhp_system_s* s) {
     A.pos_f4 = s->pos_f4;
     A.pos_d = s->pos_d;
     A.dev_max = s->dev_max;
+    A.status = s->status;
     A.qtb_u = s->qtb_u;
     A.qtb_v = s->qtb_v;
     A.qtb_F = s->qtb_F;

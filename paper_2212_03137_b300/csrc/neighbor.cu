@@ -167,13 +167,13 @@ __global__ void k_scan(const int* flag, const int* in, int* out, int n, int64_t 
 }
 
 __global__ void k_cell_scatter(const int* flag, int N, const int* cell, const int* cell_start, int* cell_fill,
-                               int* tmp) {
+                               int* tmp, const unsigned* status) {
     if (!*flag) return;
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= N) return;
     const int c = cell[a];
     const int slot = atomicAdd(&cell_fill[c], 1);
-    tmp[cell_start[c] + slot] = a;
+    if (QHP_IN_BOUNDS(cell_start[c] + slot, N, status)) tmp[cell_start[c] + slot] = a;
 }
 
 // Order each cell's atoms by index: rank = number of smaller indices in the cell.
@@ -462,7 +462,8 @@ __device__ __forceinline__ int list_key(int4 e, float lo, float inv) {
 // Persistent grid: a block sorts rows blockIdx.x, + gridDim.x, ... (so a step without a rebuild
 // costs one small launch, not one block per row).
 __global__ void __launch_bounds__(LS_THREADS) k_list_sort(const int* flag, int N, const int* start, const int* count,
-                                                          int4* nbr, int* nO, float lo, float inv) {
+                                                          int4* nbr, int* nO, float lo, float inv,
+                                                          const unsigned* status) {
     if (!*flag) return;
     extern __shared__ int4 row[];
     __shared__ int hist[LS_WARPS][LS_KEYS];   // key counts per quarter, then each quarter's first slot per key
@@ -528,7 +529,8 @@ __global__ void __launch_bounds__(LS_THREADS) k_list_sort(const int* flag, int N
             const unsigned same = __match_any_sync(0xffffffffu, key);
             if (k < k1) {   // the partner word takes the entry's bucket in bits 26-30
                 const int4 out = make_int4((e.x & ~(31 << ENTRY_J_BITS)) | ((key % LIST_BUCKETS) << ENTRY_J_BITS), e.y, e.z, e.w);
-                g[hist[w][key] + __popc(same & lt)] = out;
+                const int dst = hist[w][key] + __popc(same & lt);
+                if (QHP_IN_BOUNDS(dst, n, status)) g[dst] = out;
             }
             __syncwarp();
             if (k < k1 && (same & lt) == 0u) hist[w][key] += __popc(same);
@@ -591,7 +593,7 @@ cudaError_t launch_rebuild(qhp_system_s* s) {
         k_cells<<<gN, tb, 0, st>>>(flag, N, s->P, s->Q, s->L, s->n_c, 1, s->anchor, s->cell, s->cell_count,
                                    s->keep_anchor);
         k_scan<<<1, 1024, 0, st>>>(flag, s->cell_count, s->cell_start, ncell, -1, nullptr, s->status);
-        k_cell_scatter<<<gN, tb, 0, st>>>(flag, N, s->cell, s->cell_start, s->cell_fill, s->tmp_idx);
+        k_cell_scatter<<<gN, tb, 0, st>>>(flag, N, s->cell, s->cell_start, s->cell_fill, s->tmp_idx, s->status);
         k_cell_sort<<<ncell, 128, 0, st>>>(flag, s->cell_start, s->tmp_idx, s->perm, s->iperm);
         s->launches += 6;
     } else {
@@ -617,7 +619,7 @@ cudaError_t launch_rebuild(qhp_system_s* s) {
     float blo, binv;
     list_bucket_params(s, &blo, &binv);
     k_list_sort<<<std::min(N, s->sort_grid), LS_THREADS, sizeof(int4) * (size_t)s->row_cap, st>>>(
-        flag, N, s->nbr_start, s->nbr_count, s->nbr, s->nbr_nO, blo, binv);
+        flag, N, s->nbr_start, s->nbr_count, s->nbr, s->nbr_nO, blo, binv, s->status);
     s->launches += 3;
     return cudaGetLastError();
 }
@@ -637,7 +639,7 @@ int host_list_size(qhp_system_s* s, int64_t* max_row) {
         k_cells<<<gN, tb, 0, st>>>(flag, N, s->P, s->Q, s->L, s->n_c, 1, s->anchor, s->cell, s->cell_count,
                                    s->keep_anchor);
         k_scan<<<1, 1024, 0, st>>>(flag, s->cell_count, s->cell_start, ncell, -1, nullptr, s->status);
-        k_cell_scatter<<<gN, tb, 0, st>>>(flag, N, s->cell, s->cell_start, s->cell_fill, s->tmp_idx);
+        k_cell_scatter<<<gN, tb, 0, st>>>(flag, N, s->cell, s->cell_start, s->cell_fill, s->tmp_idx, s->status);
         k_cell_sort<<<ncell, 128, 0, st>>>(flag, s->cell_start, s->tmp_idx, s->perm, s->iperm);
     } else {
         k_cells<<<gN, tb, 0, st>>>(flag, N, s->P, s->Q, s->L, 1, 0, s->anchor, nullptr, nullptr, s->keep_anchor);

@@ -38,7 +38,24 @@ enum : unsigned {
     ST_NONFINITE = 2u,
     ST_TIMEOUT = 4u,
     ST_SPREAD = 8u,   // after a rebuild some bead lies farther than skin/2 from its anchor
+    ST_BOUNDS = 16u,  // (QHP_CHECK builds) an index read from device data was out of range
 };
+
+// Bounds checks of the QHP_CHECK build (-DQHP_CHECK; build(check=True)): an index read from
+// device data (a list partner, a permutation, a cell or row position) is tested before use;
+// an index out of range sets ST_BOUNDS in the status word and the access is skipped, with no
+// trap, so the host reports QHP_ERR_BOUNDS at the next synchronising call.  Plain builds
+// compile the test away.
+#ifdef QHP_CHECK
+__device__ __forceinline__ bool qhp_in_bounds(long long i, long long n, const unsigned* status) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(const_cast<unsigned*>(status), ST_BOUNDS);
+    return false;
+}
+#define QHP_IN_BOUNDS(i, n, status) ::qhp::qhp_in_bounds((long long)(i), (long long)(n), (status))
+#else
+#define QHP_IN_BOUNDS(i, n, status) true
+#endif
 
 // Philox4x32-10 counter tags (same definition as the oracle, written independently).
 enum : uint32_t { TAG_INIT_Q = 1, TAG_INIT_P = 2, TAG_OSTEP = 3, TAG_QTB_WHITE = 4 };

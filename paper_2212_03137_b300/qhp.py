@@ -14,11 +14,12 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libqhp.so")
+# QHP_LIBRARY selects another build of the library (the bounds-checked libqhp_check.so)
+LIB_PATH = os.environ.get("QHP_LIBRARY") or os.path.join(_HERE, "libqhp.so")
 
 QHP_OK = 0
 ERRORS = {-1: "QHP_ERR_ARG", -2: "QHP_ERR_CUDA", -3: "QHP_ERR_TIMEOUT", -4: "QHP_ERR_NONFINITE",
-          -5: "QHP_ERR_LIST_OVERFLOW", -6: "QHP_ERR_STATE", -7: "QHP_ERR_NOMEM"}
+          -5: "QHP_ERR_LIST_OVERFLOW", -6: "QHP_ERR_STATE", -7: "QHP_ERR_NOMEM", -8: "QHP_ERR_BOUNDS"}
 QHP_FP64, QHP_MIXED = 0, 1
 QHP_THERMO_PILE, QHP_THERMO_ADQTB, QHP_THERMO_NVE = 0, 1, 2
 QHP_ADAPT_NONE, QHP_ADAPT_SIMPLE, QHP_ADAPT_RATIO = 0, 1, 2
