@@ -63,6 +63,62 @@ def _dist():
     return ws, rank, local
 
 
+class _NvmlCtypes:
+    """The few NVML calls the clock sampler makes, through ctypes on the driver's
+    libnvidia-ml.so.1, for hosts without the pynvml module.  Names, signatures and the
+    clock-event reason bits follow the public nvml.h."""
+
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} returned {rc}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2(), "nvmlInit_v2")
+
+    def nvmlShutdown(self):
+        self.lib.nvmlShutdown()
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.c.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.c.c_uint(i), self.c.byref(h)), "GetHandleByIndex")
+        return h
+
+    def nvmlDeviceGetHandleByUUID(self, uuid):
+        h = self.c.c_void_p()
+        u = uuid if isinstance(uuid, bytes) else uuid.encode()
+        self._ok(self.lib.nvmlDeviceGetHandleByUUID(self.c.c_char_p(u), self.c.byref(h)), "GetHandleByUUID")
+        return h
+
+    def _clock(self, fn, h, kind):
+        v = self.c.c_uint()
+        self._ok(fn(h, self.c.c_int(kind), self.c.byref(v)), "clock query")
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo, h, kind)
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo, h, kind)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.c.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._ok(fn(h, self.c.byref(v)), "clock event reasons")
+        return v.value
+
+
 class ClockSampler:
     """SM clock and throttle-reason samples during the timed region: NVML polled every 2 ms
     from a thread (a timed region of a few milliseconds still gets samples), else nvidia-smi
@@ -96,7 +152,10 @@ class ClockSampler:
     def __enter__(self):
         self.stop = threading.Event()
         try:
-            import pynvml as nv
+            try:
+                import pynvml as nv
+            except ImportError:
+                nv = _NvmlCtypes()
             nv.nvmlInit()
             idx = self.index
             if idx.isdigit():
@@ -156,7 +215,8 @@ class ClockSampler:
         reasons = sorted({names[k] for r in self.rows for k in range(4) if r[2 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows),
-                "source": "nvml, 2 ms" if getattr(self, "nvml", None) is not None else "nvidia-smi, 50 ms",
+                "source": ("nvml, 2 ms" if getattr(self, "nvml", None) is not None else "nvidia-smi, 50 ms")
+                + (" (ctypes)" if isinstance(getattr(self, "nvml", None), _NvmlCtypes) else ""),
                 **({"nvml_error": self.nvml_error} if getattr(self, "nvml_error", None) else {})}
 
 
@@ -449,7 +509,8 @@ def run_batch(args, ws, rank, local):
             "atom_beads_per_step": units_step,
             "tuned_warps_per_atom": {str(k): v for k, v in tuned.items()},
             "launch": "one CUDA graph per batched step",
-            "roofline": {"kernel": "batched nonbonded pair kernel", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": "batched force kernel (pair and bonded items; FLOPs count the pairs)",
+                         "bound": "alu", "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": _profile_traffic("pair", "batch_256"), "pairs_per_launch": pairs,
                          "oo_pairs_per_launch": oo, "flops_per_launch": flops, "mean_launch_ms": float(st[2]),
@@ -457,8 +518,8 @@ def run_batch(args, ws, rank, local):
                          "peak_source": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} clock)"},
             "clocks": clk.summary(),
             "gpu_launches": int(i1.kernel_launches - i0.kernel_launches),
-            "stage_ms": dict(zip(["integrate_transform", "list_check_rebuild", "pair", "bonded", "project_kick"],
-                                 [round(float(x), 5) for x in st])),
+            "stage_ms": dict(zip(["integrate_transform_check", "list_rebuild", "forces", "bonded (in forces)",
+                                  "project_kick"], [round(float(x), 5) for x in st])),
             "list_rebuilds": int(i1.rebuilds - i0.rebuilds),
         }
     if args.e2e:

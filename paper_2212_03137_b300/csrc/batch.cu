@@ -1,17 +1,18 @@
 // Many independent systems stepped together (the paper's bead parallelism taken one level
 // further: systems of uneven size and bead count share every launch).
 //
-// One batched step is one CUDA graph:
-//   k_integrate_batch  B-A-O-A and bead positions of every system (persistent grid)
-//   k_check_batch      every system's displacement check; sets its conditional node
+// One batched step is one CUDA graph of three launches plus the rebuild bodies:
+//   k_integrate_batch  B-A-O-A and bead positions of every system, bead forces cleared; the
+//                      block that finishes a system's last item runs its displacement check
+//                      and sets its conditional node
 //   n_sys IF nodes     each system's list rebuild chain, run only when its check fired
-//   k_pair_batch<P>    nonbonded forces, one persistent launch per bead count present
-//                      (the item's warps per atom and list mode select the specialisation)
-//   k_bonded_batch     bonded forces
+//   k_force_batch      nonbonded and bonded forces of every system in one persistent launch
+//                      (each item selects its pair specialisation - bead count, small-box
+//                      path, warps per atom - or the bonded terms); int64 atomic adds
 //   k_project_batch    force projection and closing B
 // A persistent grid walks (system, block) items in system order; the host scheduler
 // cuts the item list into one contiguous range per resident block with about equal
-// estimated work (bead-pair work of the list rows for the pair stage), so uneven systems
+// estimated work (bead-pair work of the list rows for the pair items), so uneven systems
 // balance and a block keeps its system's transform in shared memory across items.
 //
 // The autotuner times the pair kernel of one system per bead count with 1, 2 and 4 warps
@@ -28,9 +29,11 @@ struct qhp_batch_s {
     std::vector<qhp_sys> sys;
     std::vector<cudaStream_t> sys_streams;   // the members' streams before they joined
     cudaStream_t own_stream = nullptr, stream = nullptr, aux = nullptr;
-    qhp::BatchStage integrate, bonded, project;
-    qhp::BatchStage pair[qhp::BATCH_PAIR_STAGES];   // one per (bead count, small-box path, warps per atom)
+    qhp::BatchStage integrate, force, project;
     qhp::CheckArgs* check_args = nullptr;   // device [n_sys]
+    int* done = nullptr;                    // device [n_sys]: integrate items finished this step
+    int* nitems = nullptr;                  // device [n_sys]: integrate items per system
+    int items_pair = 0;
     cudaGraphExec_t exec = nullptr;
     std::vector<int4*> nbr_seen;            // list buffers the stages were built for
     std::vector<int> rowcap_seen;
@@ -39,7 +42,7 @@ struct qhp_batch_s {
     int64_t launches = 0;
     int kernels_per_step = 0;
     std::vector<int> kernels_per_rebuild;
-    cudaEvent_t ev[6] = {};                 // stage timestamps of the last replayed step
+    cudaEvent_t ev[5] = {};                 // stage timestamps of the last replayed step
 };
 
 namespace qhp {
@@ -88,6 +91,58 @@ int stage_upload(BatchStage& st, const void* args, size_t args_bytes, const std:
     return QHP_OK;
 }
 
+int stage_upload_phased(BatchStage& st, const void* args, size_t args_bytes, const std::vector<int2>& items,
+                        const std::vector<double>& cost, const std::vector<int>& phase, int grid) {
+    const int n = (int)items.size();
+    grid = std::max(1, std::min(grid, n));
+    int n_phase = 0;
+    for (int p : phase) n_phase = std::max(n_phase, p + 1);
+    // per phase, its items in order and the cut into `grid` chunks of about equal cost
+    std::vector<std::vector<int>> idx(n_phase);
+    for (int i = 0; i < n; ++i) idx[phase[i]].push_back(i);
+    std::vector<std::vector<int>> cut(n_phase);
+    for (int p = 0; p < n_phase; ++p) {
+        const std::vector<int>& ix = idx[p];
+        double total = 0.0;
+        for (int i : ix) total += cost[i];
+        std::vector<int>& r = cut[p];
+        r.assign(grid + 1, (int)ix.size());
+        r[0] = 0;
+        double acc = 0.0;
+        int g = 1;
+        for (int k = 0; k < (int)ix.size() && g < grid; ++k) {
+            acc += cost[ix[k]];
+            while (g < grid && acc >= total * (double)g / (double)grid) r[g++] = k + 1;
+        }
+    }
+    // block g runs chunk g of every phase, phase by phase
+    std::vector<int2> out;
+    out.reserve(n);
+    std::vector<int> ranges(grid + 1, 0);
+    double total = 0.0;
+    for (int g = 0; g < grid; ++g) {
+        for (int p = 0; p < n_phase; ++p)
+            for (int k = cut[p][g]; k < cut[p][g + 1]; ++k) {
+                out.push_back(items[idx[p][k]]);
+                total += cost[idx[p][k]];
+            }
+        ranges[g + 1] = (int)out.size();
+    }
+    const size_t smem = st.smem;
+    stage_free(st);
+    st.smem = smem;
+    st.grid = grid;
+    st.n_items = n;
+    st.cost = total;
+    QHP_CUDA(cudaMalloc(&st.args, std::max<size_t>(args_bytes, 1)));
+    QHP_CUDA(cudaMalloc(&st.items, sizeof(int2) * std::max(n, 1)));
+    QHP_CUDA(cudaMalloc(&st.ranges, sizeof(int) * (grid + 1)));
+    QHP_CUDA(cudaMemcpy(st.args, args, args_bytes, cudaMemcpyHostToDevice));
+    QHP_CUDA(cudaMemcpy(st.items, out.data(), sizeof(int2) * n, cudaMemcpyHostToDevice));
+    QHP_CUDA(cudaMemcpy(st.ranges, ranges.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice));
+    return QHP_OK;
+}
+
 namespace {
 
 void drop_graph(qhp_batch_s* b) {
@@ -100,8 +155,7 @@ std::vector<qhp_system_s*> members(qhp_batch_s* b) { return std::vector<qhp_syst
 int build_stages(qhp_batch_s* b) {
     const std::vector<qhp_system_s*> v = members(b);
     TRY(batch_stage_integrate(v, b->integrate));
-    TRY(batch_stage_pair(v, b->pair));
-    TRY(batch_stage_bonded(v, b->bonded));
+    TRY(batch_stage_force(v, b->force, &b->items_pair));
     TRY(batch_stage_project(v, b->project));
     b->nbr_seen.clear();
     b->rowcap_seen.clear();
@@ -134,7 +188,13 @@ int capture(qhp_batch_s* b) {
         ca[k] = CheckArgs{s->dev_max, s->rebuild_flag, s->rebuild_count, handles[k], half * half};
     }
     if (!b->check_args) QHP_CUDA(cudaMalloc(&b->check_args, sizeof(CheckArgs) * n));
+    if (!b->done) QHP_CUDA(cudaMalloc(&b->done, sizeof(int) * n));
+    if (!b->nitems) QHP_CUDA(cudaMalloc(&b->nitems, sizeof(int) * n));
+    std::vector<int> ni(n);
+    for (int k = 0; k < n; ++k) ni[k] = batch_integrate_items(b->sys[k]);
     QHP_CUDA(cudaMemcpy(b->check_args, ca.data(), sizeof(CheckArgs) * n, cudaMemcpyHostToDevice));
+    QHP_CUDA(cudaMemcpy(b->nitems, ni.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    QHP_CUDA(cudaMemset(b->done, 0, sizeof(int) * n));
 
     cudaError_t e = cudaStreamBeginCaptureToGraph(b->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
@@ -150,10 +210,9 @@ int capture(qhp_batch_s* b) {
     // event-record nodes between the stages: every replay timestamps them
     auto mark = [&](int k) { fail(cudaEventRecordWithFlags(b->ev[k], b->stream, cudaEventRecordExternal), "batch event"); };
     mark(0);
-    fail(launch_batch_integrate(b->integrate, b->stream), "batch integrate");
+    fail(launch_batch_integrate(b->integrate, b->check_args, b->done, b->nitems, b->stream), "batch integrate");
     mark(1);
-    fail(launch_check_batch(b->check_args, n, b->stream), "batch check");
-    kernels += 2;
+    kernels += 1;
     std::vector<cudaGraphNode_t> conds(n);
     if (rc == QHP_OK) {
         cudaStreamCaptureStatus cs;
@@ -198,13 +257,10 @@ int capture(qhp_batch_s* b) {
                  "batch join");
     }
     mark(2);
-    fail(launch_batch_pair(b->pair, b->stream), "batch pair");
+    fail(launch_batch_force(b->force, b->stream), "batch forces");
     mark(3);
-    fail(launch_batch_bonded(b->bonded, b->stream), "batch bonded");
-    mark(4);
     fail(launch_batch_project(b->project, b->stream), "batch project");
-    mark(5);
-    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) kernels += b->pair[k].n_items > 0 ? 1 : 0;
+    mark(4);
     kernels += 2;
     cudaGraph_t g2 = nullptr;
     e = cudaStreamEndCapture(b->stream, &g2);
@@ -340,7 +396,7 @@ int qhp_create_batch(qhp_batch* out, int n_sys, const qhp_sys* systems) {
     int rc = QHP_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
     if (e != cudaSuccess) rc = cuda_fail(e, "batch streams");
     b->stream = b->own_stream;
     // every member starts with valid forces and list; from now on its work is queued on
@@ -370,11 +426,12 @@ int qhp_destroy_batch(qhp_batch b) {
     }
     drop_graph(b);
     stage_free(b->integrate);
-    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) stage_free(b->pair[k]);
-    stage_free(b->bonded);
+    stage_free(b->force);
     stage_free(b->project);
     cudaFree(b->check_args);
-    for (int k = 0; k < 6; ++k)
+    cudaFree(b->done);
+    cudaFree(b->nitems);
+    for (int k = 0; k < 5; ++k)
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     if (b->aux) cudaStreamDestroy(b->aux);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
@@ -460,14 +517,14 @@ int qhp_batch_get_profile(qhp_batch b, qhp_profile* out) {
         return QHP_ERR_STATE;
     }
     QHP_CUDA(cudaStreamSynchronize(b->stream));
-    float t[5];
-    for (int k = 0; k < 5; ++k) QHP_CUDA(cudaEventElapsedTime(&t[k], b->ev[k], b->ev[k + 1]));
+    float t[4];
+    for (int k = 0; k < 4; ++k) QHP_CUDA(cudaEventElapsedTime(&t[k], b->ev[k], b->ev[k + 1]));
     out->integrate_ms = t[0];
     out->list_ms = t[1];
-    out->pair_ms = t[2];
-    out->bonded_ms = t[3];
-    out->project_ms = t[4];
-    out->step_ms = t[0] + t[1] + t[2] + t[3] + t[4];
+    out->pair_ms = t[2];   // the merged force stage: pair and bonded items
+    out->bonded_ms = 0.0f;
+    out->project_ms = t[3];
+    out->step_ms = t[0] + t[1] + t[2] + t[3];
     return QHP_OK;
 }
 
@@ -479,10 +536,10 @@ int qhp_batch_get_info(qhp_batch b, qhp_batch_info* out) {
     out->steps = b->steps;
     out->kernels_per_step = b->kernels_per_step;
     out->grid_integrate = b->integrate.grid;
-    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) out->grid_pair += b->pair[k].grid;
-    out->grid_bonded = b->bonded.grid;
+    out->grid_pair = b->force.grid;   // pair and bonded items share the force launch
+    out->grid_bonded = 0;
     out->grid_project = b->project.grid;
-    for (int k = 0; k < BATCH_PAIR_STAGES; ++k) out->items_pair += b->pair[k].n_items;
+    out->items_pair = b->items_pair;
     // kernels run inside the conditional rebuild bodies, counted on the device
     cudaStreamSynchronize(b->stream);
     int64_t extra = 0;

@@ -395,7 +395,7 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
 // A block's FP32 sum is converted to int64 once and the integers are added, so the forces do
 // not depend on W.  Entries beyond rc + 2 max|x_ib - A_i| (+ margin) of every bead pair are
 // skipped (pair_group): they would add exactly zero.
-template <int P, int W, bool ALL, bool ENERGY>
+template <int P, int W, bool ALL, bool ENERGY, bool ACC = false>
 __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& sm) {
     constexpr bool ONE = P == 1;
     constexpr int LPE = ONE ? 1 : P / 2;
@@ -467,8 +467,14 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& s
                 if (!ONE) s1 += sm.acc[w + v][d][2 * bp + 1];
             }
             long long* out = A.F + ((size_t)a * 3 + d) * P + 2 * bp;
-            if (ONE) out[0] = s0;
-            else *reinterpret_cast<longlong2*>(out) = make_longlong2(s0, s1);
+            if (ACC) {   // batched step: integer adds into forces cleared by the integrate stage
+                atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)s0);
+                if (!ONE) atomicAdd(reinterpret_cast<unsigned long long*>(out + 1), (unsigned long long)s1);
+            } else if (ONE) {
+                out[0] = s0;
+            } else {
+                *reinterpret_cast<longlong2*>(out) = make_longlong2(s0, s1);
+            }
         }
         if (ENERGY) {
             float e0 = sm.esum[w][2 * bp], e1 = ONE ? 0.0f : sm.esum[w][2 * bp + 1];
@@ -494,25 +500,6 @@ template <int P, int W, bool ALL, bool ENERGY>
 __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_min_blocks<P>()) k_pair_mixed(const __grid_constant__ PairArgs A) {
     __shared__ PairSmem sm;
     pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, sm);
-}
-
-// Batched systems: one persistent launch per (bead count, small-box path, warps per atom)
-// present, over the (system, block) items of the systems of that kind.  Each launch carries
-// one specialisation, so it runs at that specialisation's registers and residency (the same
-// as the single-system kernel).
-template <int P>
-__host__ __device__ constexpr int pair_batch_min_blocks() { return 0; }
-
-template <int P, int W, bool ALL>
-__global__ void __launch_bounds__(32 * PAIR_WARPS, pair_batch_min_blocks<P>()) k_pair_batch(const PairArgs* __restrict__ args,
-                                                                                      const int2* __restrict__ items,
-                                                                                      const int* __restrict__ ranges) {
-    __shared__ PairSmem sm;
-    for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
-        const int2 w = items[it];
-        __syncthreads();   // the previous item's sums have been read
-        pair_body<P, W, ALL, false>(args[w.x], w.y, sm);
-    }
 }
 
 // FP64 path, small boxes: one warp per (sorted atom i, bead b), its lanes over i's list row,
@@ -689,7 +676,7 @@ struct BondArgs {
     const unsigned* status;
 };
 
-template <bool MIXED, bool ENERGY>
+template <bool MIXED, bool ENERGY, bool ACC = false>
 __device__ __forceinline__ void bonded_body(const BondArgs& A, int t) {
     const int n_mol = A.n_mol, N = A.N, P = A.P;
     const float4* __restrict__ pos_f = A.pos_f;
@@ -737,6 +724,11 @@ __device__ __forceinline__ void bonded_body(const BondArgs& A, int t) {
                 Ffix[((size_t)aH1 * 3 + d) * P + b] = i1;
                 Ffix[((size_t)aH2 * 3 + d) * P + b] = i2;
                 Ffix[((size_t)aO * 3 + d) * P + b] = -(i1 + i2);
+            } else if (ACC) {   // batched step: the pair terms of the same atoms add concurrently
+                atomicAdd(reinterpret_cast<unsigned long long*>(&Ffix[((size_t)aH1 * 3 + d) * P + b]), (unsigned long long)i1);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&Ffix[((size_t)aH2 * 3 + d) * P + b]), (unsigned long long)i2);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&Ffix[((size_t)aO * 3 + d) * P + b]),
+                          (unsigned long long)(-(i1 + i2)));
             } else {
                 Ffix[((size_t)aH1 * 3 + d) * P + b] += i1;
                 Ffix[((size_t)aH2 * 3 + d) * P + b] += i2;
@@ -782,13 +774,57 @@ __global__ void k_bonded(const __grid_constant__ BondArgs A) {
     bonded_body<MIXED, ENERGY>(A, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-__global__ void k_bonded_batch(const BondArgs* __restrict__ args, const int2* __restrict__ items,
-                               const int* __restrict__ ranges) {
+// Force stage of a batched step: one persistent launch over the items of every system - pair
+// items of every (bead count, small-box path, warps per atom) specialisation and bonded items -
+// in one grid.  Both add int64 fixed-point forces atomically into the forces the integrate
+// stage cleared: integer addition is exact, so the order of the items (and which block runs
+// which) cannot change a bit, and the sums equal a single system's store-then-add.
+struct ForceArgs {
+    PairArgs p;
+    BondArgs b;
+};
+
+// Item kind: batch_pair_stage(log2 P, small-box path, W) for pair items, FORCE_BONDED_VARIANT
+// for bonded ones.
+__host__ __device__ constexpr int batch_pair_stage(int lp, int all, int W) {
+    return (lp * 2 + all) * 3 + (W == 4 ? 2 : W == 2 ? 1 : 0);
+}
+
+#define QHP_FORCE_CASE(LP, AL, WS)                                                                        \
+    case ((LP) * 2 + (AL)) * 3 + (WS):                                                                   \
+        pair_body<(1 << (LP)), ((WS) == 2 ? 4 : (WS) == 1 ? 2 : 1), ((AL) != 0), false, true>(A.p, bx, sm); \
+        break;
+#define QHP_FORCE_CASES_W(LP, AL) QHP_FORCE_CASE(LP, AL, 0) QHP_FORCE_CASE(LP, AL, 1) QHP_FORCE_CASE(LP, AL, 2)
+#define QHP_FORCE_CASES_P(LP) QHP_FORCE_CASES_W(LP, 0) QHP_FORCE_CASES_W(LP, 1)
+
+// 8 resident blocks (64 registers): the 42 inlined specialisations and the per-item arguments,
+// read from global memory rather than the parameter bank, spill heavily at 12 blocks (40).
+#ifndef QHP_FORCE_BATCH_MIN_BLOCKS
+#define QHP_FORCE_BATCH_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(32 * PAIR_WARPS, QHP_FORCE_BATCH_MIN_BLOCKS) k_force_batch(const ForceArgs* __restrict__ args,
+                                                                   const int2* __restrict__ items,
+                                                                   const int* __restrict__ ranges) {
+    __shared__ PairSmem sm;
     for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
         const int2 w = items[it];
-        bonded_body<true, false>(args[w.x], w.y * (int)blockDim.x + threadIdx.x);
+        const int sys = w.x & 0xffff, kind = w.x >> 16, bx = w.y;
+        const ForceArgs& A = args[sys];
+        __syncthreads();   // the previous item's sums have been read
+        if (kind == FORCE_BONDED_VARIANT) {
+            bonded_body<true, false, true>(A.b, bx * (int)blockDim.x + threadIdx.x);
+            continue;
+        }
+        switch (kind) {
+            QHP_FORCE_CASES_P(0) QHP_FORCE_CASES_P(1) QHP_FORCE_CASES_P(2) QHP_FORCE_CASES_P(3)
+            QHP_FORCE_CASES_P(4) QHP_FORCE_CASES_P(5) QHP_FORCE_CASES_P(6)
+            default: break;
+        }
     }
 }
+#undef QHP_FORCE_CASE
+#undef QHP_FORCE_CASES_W
+#undef QHP_FORCE_CASES_P
 
 // Count in-cutoff bead pairs j > i (lane = bead, one list entry at a time); not on the step path.
 __global__ void k_count_pairs(int N, int P, int mixed, int all, const float4* __restrict__ pos_f,
@@ -1049,121 +1085,71 @@ cudaError_t launch_bonded(qhp_system_s* s, bool energy) {
     return cudaGetLastError();
 }
 
-// Batched stages (mixed precision).  Pair items are blocks of PAIR_WARPS / W atoms, costed
-// by the bead-pair work of their list rows (row length x max(P, 32) lanes); one stage per
-// (log2 P, small-box path, W), index batch_pair_stage(lp, all, W).
-int batch_pair_stage(int lp, int all, int W) { return (lp * 2 + all) * 3 + (W == 4 ? 2 : W == 2 ? 1 : 0); }
-
-template <int P>
-struct PairBatchVariants {
-    template <int W, bool ALL>
-    static void go(const BatchStage* s, cudaStream_t st, const void** ptr) {
-        if (ptr) *ptr = (const void*)k_pair_batch<P, W, ALL>;
-        else k_pair_batch<P, W, ALL><<<s->grid, 32 * PAIR_WARPS, 0, st>>>((const PairArgs*)s->args, s->items, s->ranges);
+// The batched force stage (mixed precision): pair items are blocks of PAIR_WARPS / W atoms,
+// costed by the warp passes of their list rows (a pass evaluates 32 / max(1, P/2) entries);
+// bonded items are blocks of 128 (molecule, bead) pairs.  Every resident block gets an equal
+// share of every specialisation's items, specialisation by specialisation.
+int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* n_pair_items) {
+    if (v.size() > 0xffff) {
+        set_error("a batch holds at most 65535 systems");
+        return QHP_ERR_ARG;
     }
-    // launch stage s (ptr == nullptr) or return its kernel (ptr != nullptr)
-    static void dispatch(int all, int W, const BatchStage* s, cudaStream_t st, const void** ptr) {
-        if (all) {
-            if (W == 4) go<4, true>(s, st, ptr);
-            else if (W == 2) go<2, true>(s, st, ptr);
-            else go<1, true>(s, st, ptr);
-        } else {
-            if (W == 4) go<4, false>(s, st, ptr);
-            else if (W == 2) go<2, false>(s, st, ptr);
-            else go<1, false>(s, st, ptr);
-        }
-    }
-};
-
-void pair_batch_dispatch(int lp, int all, int W, const BatchStage* s, cudaStream_t st, const void** ptr) {
-    switch (lp) {
-        case 0: PairBatchVariants<1>::dispatch(all, W, s, st, ptr); break;
-        case 1: PairBatchVariants<2>::dispatch(all, W, s, st, ptr); break;
-        case 2: PairBatchVariants<4>::dispatch(all, W, s, st, ptr); break;
-        case 3: PairBatchVariants<8>::dispatch(all, W, s, st, ptr); break;
-        case 4: PairBatchVariants<16>::dispatch(all, W, s, st, ptr); break;
-        case 5: PairBatchVariants<32>::dispatch(all, W, s, st, ptr); break;
-        default: PairBatchVariants<64>::dispatch(all, W, s, st, ptr); break;
-    }
-}
-
-int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[BATCH_PAIR_STAGES]*/) {
-    const int Ws[3] = {1, 2, 4};
-    for (int lp = 0; lp < 7; ++lp)
-        for (int all = 0; all < 2; ++all)
-            for (int W : Ws) {
-                const int P = 1 << lp;
-                BatchStage& S = st[batch_pair_stage(lp, all, W)];
-                std::vector<PairArgs> a;
-                std::vector<int2> items;
-                std::vector<double> cost;
-                for (size_t k = 0; k < v.size(); ++k) {
-                    const qhp_system_s* s = v[k];
-                    if (s->P != P) continue;
-                    const PairArgs A = make_pair_args(s);
-                    if (A.all != all || A.W != W) continue;
-                    const int idx = (int)a.size();
-                    a.push_back(A);
-                    const int apb = PAIR_WARPS / W;
-                    const int nb = (s->N + apb - 1) / apb;
-                    std::vector<int> cnt(s->N);
-                    QHP_CUDA(cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * s->N, cudaMemcpyDeviceToHost));
-                    const double lanes = (double)std::max(P, 32) / 32.0;
-                    for (int b = 0; b < nb; ++b) {
-                        double c = 0.0;
-                        for (int i = b * apb; i < std::min(s->N, (b + 1) * apb); ++i) c += (double)cnt[i] * lanes;
-                        items.push_back(make_int2(idx, b));
-                        cost.push_back(c + 8.0);
-                    }
-                }
-                if (a.empty()) {
-                    stage_free(S);
-                    continue;
-                }
-                const void* fn = nullptr;
-                pair_batch_dispatch(lp, all, W, nullptr, nullptr, &fn);
-                int per_sm = 0;
-                QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * PAIR_WARPS, 0));
-                S.smem = 0;
-                TRY(stage_upload(S, a.data(), sizeof(PairArgs) * a.size(), items, cost, std::max(1, per_sm) * sm_count()));
-            }
-    return QHP_OK;
-}
-
-int batch_stage_bonded(const std::vector<qhp_system_s*>& v, BatchStage& st) {
-    std::vector<BondArgs> a;
+    std::vector<ForceArgs> a;
     std::vector<int2> items;
     std::vector<double> cost;
     for (size_t k = 0; k < v.size(); ++k) {
-        a.push_back(make_bond_args(v[k]));
-        const int nb = (v[k]->n_mol * v[k]->P + 127) / 128;
+        const qhp_system_s* s = v[k];
+        ForceArgs fa;
+        fa.p = make_pair_args(s);
+        fa.b = make_bond_args(s);
+        a.push_back(fa);
+        const int P = s->P, W = fa.p.W, lp = __builtin_ctz((unsigned)P);
+        const int kind = batch_pair_stage(lp, fa.p.all, W);
+        const int apb = PAIR_WARPS / W;
+        const int nb = (s->N + apb - 1) / apb;
+        std::vector<int> cnt(s->N);
+        QHP_CUDA(cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * s->N, cudaMemcpyDeviceToHost));
+        // warp passes per entry: a pass evaluates 32 / LPE entries, LPE = max(1, P / 2) lanes each
+        const double passes = (double)std::max(1, P / 2) / 32.0;
         for (int b = 0; b < nb; ++b) {
-            items.push_back(make_int2((int)k, b));
+            double c = 0.0;
+            for (int i = b * apb; i < std::min(s->N, (b + 1) * apb); ++i) c += (double)cnt[i] * passes;
+            items.push_back(make_int2((kind << 16) | (int)k, b));
+            cost.push_back(c / PAIR_WARPS + 2.0);   // per warp of the block, plus the row set-up and sums
+        }
+        const int nbb = (s->n_mol * P + 127) / 128;
+        for (int b = 0; b < nbb; ++b) {
+            items.push_back(make_int2((FORCE_BONDED_VARIANT << 16) | (int)k, b));
             cost.push_back(1.0);
         }
     }
+    if (n_pair_items) {
+        *n_pair_items = 0;
+        for (const int2& w : items) *n_pair_items += (w.x >> 16) != FORCE_BONDED_VARIANT;
+    }
     int per_sm = 0;
-    QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bonded_batch, 128, 0));
+    QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_batch, 32 * PAIR_WARPS, 0));
     st.smem = 0;
-    return stage_upload(st, a.data(), sizeof(BondArgs) * a.size(), items, cost, std::max(1, per_sm) * sm_count());
+    const int grid = std::max(1, per_sm) * sm_count();
+#ifdef QHP_FORCE_BATCH_FLAT
+    return stage_upload(st, a.data(), sizeof(ForceArgs) * a.size(), items, cost, grid);
+#else
+    // one phase per specialisation present (in kind order, bonded last): the blocks of an SM run
+    // the same code at about the same time instead of a mix of the 43 bodies
+    std::vector<int> kinds;
+    for (const int2& w : items) kinds.push_back(w.x >> 16);
+    std::vector<int> uniq(kinds);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    std::vector<int> phase(items.size());
+    for (size_t i = 0; i < items.size(); ++i)
+        phase[i] = (int)(std::lower_bound(uniq.begin(), uniq.end(), kinds[i]) - uniq.begin());
+    return stage_upload_phased(st, a.data(), sizeof(ForceArgs) * a.size(), items, cost, phase, grid);
+#endif
 }
 
-cudaError_t launch_batch_pair(const BatchStage* st, cudaStream_t stream) {
-    const int Ws[3] = {1, 2, 4};
-    for (int lp = 0; lp < 7; ++lp)
-        for (int all = 0; all < 2; ++all)
-            for (int W : Ws) {
-                const BatchStage& S = st[batch_pair_stage(lp, all, W)];
-                if (S.n_items == 0) continue;
-                pair_batch_dispatch(lp, all, W, &S, stream, nullptr);
-                const cudaError_t e = cudaGetLastError();
-                if (e != cudaSuccess) return e;
-            }
-    return cudaSuccess;
-}
-
-cudaError_t launch_batch_bonded(const BatchStage& st, cudaStream_t stream) {
-    k_bonded_batch<<<st.grid, 128, 0, stream>>>((const BondArgs*)st.args, st.items, st.ranges);
+cudaError_t launch_batch_force(const BatchStage& st, cudaStream_t stream) {
+    k_force_batch<<<st.grid, 32 * PAIR_WARPS, 0, stream>>>((const ForceArgs*)st.args, st.items, st.ranges);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ struct IntegrateArgs {
     const double* fmode_s; // RESPA: slow mode forces kicked together with the fast ones
     double ws;             //        with weight ws (n_alt on the first inner step, else 0)
     const unsigned* status;
+    long long* fzero;      // batched step: bead forces cleared here, before the forces add into them
 };
 
 __device__ __forceinline__ void block_max_atomic(float v, unsigned* out) {
@@ -177,6 +178,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
             free_half(n, c, q, pm);                                   // A
             A.Q[idx] = q;
             A.Pm[idx] = pm;
+            if (A.fzero) A.fzero[idx] = 0;
         }
     }
     qs[t] = q;
@@ -229,9 +231,30 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(const __grid_constant__ Int
 
 // Batched systems: a persistent grid, each block walking its contiguous range of
 // (system, atom-group) items; the transform is restaged only when the system changes.
+// The list check of one system (the single-system k_check): clear the deviation maximum and
+// count the rebuild when it fires, and set the system's conditional node.
+__device__ __forceinline__ void batch_check(const CheckArgs& a) {
+    const float dmax = __uint_as_float(atomicAdd(a.dev_max, 0u));   // coherent read of the blocks' maxima
+    const int rebuild = !(dmax <= a.thr2);                          // NaN also triggers a rebuild
+    *a.flag = rebuild;
+    if (rebuild) {
+        *a.dev_max = 0u;
+        a.rebuild_count[0] += 1u;
+        a.rebuild_count[1] += 1u;
+    }
+    cudaGraphSetConditional(a.cond, rebuild ? 1u : 0u);
+}
+
+// Head of a batched step: B-A-O-A and bead positions of every system (persistent grid over
+// (system, atom-group) items), the bead forces cleared for the force stage to add into, and
+// each system's list check run by the block that completes its last item: every block counts
+// its finished item in done[system] after a fence, and the one that brings the count to the
+// system's item count sees every other block's deviation maximum.  Nothing waits.
 __global__ void __launch_bounds__(BLOCK) k_integrate_batch(const IntegrateArgs* __restrict__ args,
                                                            const int2* __restrict__ items,
-                                                           const int* __restrict__ ranges) {
+                                                           const int* __restrict__ ranges,
+                                                           const CheckArgs* __restrict__ checks, int* done,
+                                                           const int* __restrict__ nitems) {
     extern __shared__ unsigned char smem_raw[];
     int prev = -1;
     for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
@@ -239,6 +262,17 @@ __global__ void __launch_bounds__(BLOCK) k_integrate_batch(const IntegrateArgs* 
         __syncthreads();   // the previous item is done with shared memory
         integrate_body<true, false, true>(args[w.x], w.y, smem_raw, w.x != prev);
         prev = w.x;
+        if (checks) {
+            __syncthreads();   // every thread of the item has written its modes, positions and forces
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (atomicAdd(&done[w.x], 1) == nitems[w.x] - 1) {
+                    __threadfence();
+                    batch_check(checks[w.x]);
+                    done[w.x] = 0;   // for the next step
+                }
+            }
+        }
     }
 }
 
@@ -580,6 +614,13 @@ static IntegrateArgs make_iargs(qhp_system_s* s) {
     A.gate = nullptr;
     A.fmode_s = nullptr;
     A.ws = 0.0;
+    A.fzero = nullptr;
+    return A;
+}
+
+static IntegrateArgs make_iargs_batch(qhp_system_s* s) {
+    IntegrateArgs A = make_iargs(s);
+    A.fzero = s->Ffix;
     return A;
 }
 
@@ -688,17 +729,22 @@ static int integrate_like_stage(const std::vector<qhp_system_s*>& v, BatchStage&
 }
 
 int batch_stage_integrate(const std::vector<qhp_system_s*>& v, BatchStage& st) {
-    return integrate_like_stage<IntegrateArgs>(v, st, make_iargs, (const void*)k_integrate_batch, 4);
+    return integrate_like_stage<IntegrateArgs>(v, st, make_iargs_batch, (const void*)k_integrate_batch, 4);
 }
 
 int batch_stage_project(const std::vector<qhp_system_s*>& v, BatchStage& st) {
     return integrate_like_stage<ProjectArgs>(v, st, make_pargs, (const void*)k_project_batch, 4);
 }
 
-cudaError_t launch_batch_integrate(const BatchStage& st, cudaStream_t stream) {
-    k_integrate_batch<<<st.grid, BLOCK, st.smem, stream>>>((const IntegrateArgs*)st.args, st.items, st.ranges);
+cudaError_t launch_batch_integrate(const BatchStage& st, const CheckArgs* checks, int* done, const int* nitems,
+                                   cudaStream_t stream) {
+    k_integrate_batch<<<st.grid, BLOCK, st.smem, stream>>>((const IntegrateArgs*)st.args, st.items, st.ranges, checks,
+                                                           done, nitems);
     return cudaGetLastError();
 }
+
+// Items (atom groups of 64/P atoms) of every system in the batched integrate stage.
+int batch_integrate_items(const qhp_system_s* s) { return (s->N + 64 / s->P - 1) / (64 / s->P); }
 
 cudaError_t launch_batch_project(const BatchStage& st, cudaStream_t stream) {
     k_project_batch<<<st.grid, BLOCK, st.smem, stream>>>((const ProjectArgs*)st.args, st.items, st.ranges);

@@ -78,20 +78,6 @@ __global__ void k_check(unsigned* dev_max, float thr2, int* flag, int force, uns
     }
 }
 
-__global__ void k_check_batch(const CheckArgs* __restrict__ a, int n) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const float dmax = __uint_as_float(*a[k].dev_max);
-    const int rebuild = !(dmax <= a[k].thr2);
-    *a[k].flag = rebuild;
-    if (rebuild) {
-        *a[k].dev_max = 0u;
-        a[k].rebuild_count[0] += 1u;
-        a[k].rebuild_count[1] += 1u;
-    }
-    cudaGraphSetConditional(a[k].cond, rebuild ? 1u : 0u);
-}
-
 // Right after a rebuild the deviation maximum is measured from the new anchors; the list
 // covers every bead pair within rc only if no bead lies farther than skin/2 from its anchor.
 __global__ void k_check_cover(const int* flag, const unsigned* dev_max, float thr2, unsigned* status) {
@@ -566,11 +552,6 @@ cudaError_t launch_list_check(qhp_system_s* s, bool force) {
     s->launches++;
     k_check<<<1, 1, 0, s->stream>>>(s->dev_max, half * half, s->rebuild_flag, force ? 1 : 0, s->rebuild_count,
                                     s->cond_handle, s->cond_active);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_check_batch(const CheckArgs* args, int n, cudaStream_t stream) {
-    k_check_batch<<<(n + 127) / 128, 128, 0, stream>>>(args, n);
     return cudaGetLastError();
 }
 

@@ -407,18 +407,18 @@ struct BatchStage {
 // Upload a stage: split the items into `grid` contiguous ranges of about equal cost.
 int stage_upload(BatchStage& st, const void* args, size_t args_bytes, const std::vector<int2>& items,
                  const std::vector<double>& cost, int grid);
+// Upload a stage whose items run in phases (a phase: items of one kernel specialisation): each
+// phase is cut into `grid` chunks of about equal cost and block g runs chunk g of every phase,
+// phase by phase, so at any time the blocks of the grid run about the same specialisation.
+int stage_upload_phased(BatchStage& st, const void* args, size_t args_bytes, const std::vector<int2>& items,
+                        const std::vector<double>& cost, const std::vector<int>& phase, int grid);
 void stage_free(BatchStage& st);
 int sm_count();
 int batch_stage_integrate(const std::vector<qhp_system_s*>& v, BatchStage& st);
 int batch_stage_project(const std::vector<qhp_system_s*>& v, BatchStage& st);
 constexpr int BATCH_PAIR_STAGES = 7 * 2 * 3;   // (log2 P, small-box path, W = 1, 2, 4)
-int batch_stage_pair(const std::vector<qhp_system_s*>& v, BatchStage* st /*[BATCH_PAIR_STAGES]*/);
-int batch_stage_bonded(const std::vector<qhp_system_s*>& v, BatchStage& st);
-cudaError_t launch_batch_integrate(const BatchStage& st, cudaStream_t stream);
-cudaError_t launch_batch_project(const BatchStage& st, cudaStream_t stream);
-cudaError_t launch_batch_pair(const BatchStage* st /*[BATCH_PAIR_STAGES]*/, cudaStream_t stream);   // one launch per non-empty stage
-cudaError_t launch_batch_bonded(const BatchStage& st, cudaStream_t stream);
-// Per-system record of the batched list check (the single-system k_check, one thread each).
+// Per-system record of the batched list check (the single-system k_check), run at the end of
+// the batched integrate stage by the block that completes the system's last item.
 struct CheckArgs {
     unsigned* dev_max;
     int* flag;
@@ -426,7 +426,14 @@ struct CheckArgs {
     cudaGraphConditionalHandle cond;
     float thr2;
 };
-cudaError_t launch_check_batch(const CheckArgs* args, int n, cudaStream_t stream);
+cudaError_t launch_batch_integrate(const BatchStage& st, const CheckArgs* checks, int* done, const int* nitems,
+                                   cudaStream_t stream);
+int batch_integrate_items(const qhp_system_s* s);
+constexpr int FORCE_BONDED_VARIANT = BATCH_PAIR_STAGES;   // item kind of the batched bonded terms
+int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* n_pair_items);
+cudaError_t launch_batch_force(const BatchStage& st, cudaStream_t stream);
+cudaError_t launch_batch_project(const BatchStage& st, cudaStream_t stream);
+
 int compute_energy(qhp_system_s* s, qhp_energy* out);
 int beads_fp64(qhp_system_s* s, double* dev_out);
 cudaError_t launch_estimators(qhp_system_s* s, double* partial, int* nblocks);
