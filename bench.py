@@ -228,9 +228,14 @@ def _peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
+SKIN = None   # --skin: the neighbour-list skin (A) in place of the workload's own
+
+
 def _config(name):
+    import dataclasses
     from paper_2212_03137_b300.workloads import CONFIGS
-    return CONFIGS[name]
+    cfg = CONFIGS[name]
+    return dataclasses.replace(cfg, skin=SKIN) if SKIN is not None else cfg
 
 
 def _workload_conf(name, cfg, ws):
@@ -816,8 +821,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     # kernel-by-kernel launches instead of step graphs, for profiler launch lists
     ap.add_argument("--direct-launch", action="store_true")
+    ap.add_argument("--skin", type=float, default=None, help="neighbour-list skin in A (default: the workload's)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global SKIN
+    SKIN = args.skin
     ws, rank, local = _dist()
     if ws > 1:
         import torch

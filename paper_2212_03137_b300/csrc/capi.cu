@@ -633,6 +633,7 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     if (s->precision == QHP_MIXED) {
         TRY(dalloc(s, &s->Ffix, NP3));
         TRY(dalloc(s, &s->pos_f4, (size_t)N * P));
+        TRY(dalloc(s, &s->dev_atom, (size_t)N));
         TRY(dalloc(s, &s->e_pair, (size_t)N * P));
         TRY(dalloc(s, &s->dA, (size_t)s->n_mol * 8));
     } else {
@@ -740,6 +741,7 @@ int qhp_set_respa(qhp_sys s, int n_alt, int contracted_beads) {
     if (pc != s->pc || !s->Ffix_s) {
         TRY(dalloc(s, &s->Ffix_s, (size_t)s->N * 3 * pc));
         TRY(dalloc(s, &s->pos_c, (size_t)s->N * pc));
+        if (!s->dev_atom_c) TRY(dalloc(s, &s->dev_atom_c, (size_t)s->N));
         if (!s->fmode_s) TRY(dalloc(s, &s->fmode_s, (size_t)s->N * 3 * P));
         TRY(dalloc(s, &s->Cmat_f, (size_t)pc * P));
         // C[b][n] = sqrt(P) T[b P/pc][n] on the pc lowest-frequency modes (centroid, cos/sin of

@@ -96,7 +96,9 @@ struct PairArgs {
     long long* F;
     float* epair;
     const unsigned* status;
-    const unsigned* dev_max;   // running max |x_ib - A_i|^2 since the list build, or null (no skipping)
+    const unsigned* dev_max;   // running max |x_ib - A_i|^2 since the list build, or null
+    const float* dev_atom;     // per sorted atom, max over its beads of |x_ib - A_i|^2 this step, or null
+    int skip;                  // 1: entries beyond every bead pair's reach are dropped, 0: evaluated
     PairConsts c;
 };
 
@@ -245,7 +247,10 @@ __host__ __device__ constexpr int pair_block(int P) { return P >= 16 ? 32 : (P <
 // Per-warp state of one atom's row walk.
 struct PairLane {
     float2 nxi, nyi, nzi;   // minus the lane's own two bead offsets
-    int i, slot, bp, b_stop;
+    int i, slot, bp;
+    int b_stop;             // the row walk ends at the first 32 entries from this bucket on
+    int b_act;              // entries from this bucket on lie beyond reach of every bead pair
+    float reach_i;          // rc + max_b |x_ib - A_i| (+ margin), or 0: no per-entry test
 };
 
 // Adds the FP32 sums (fx, fy, fz) of one block to the warp's int64 accumulators: the slots
@@ -352,32 +357,69 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
             for (int sb = kb; sb < bend; sb += 32) {
                 const int n = min(32, bend - sb);
                 int4 e = make_int4(0, 0, 0, 0);
-                bool active = false;
+                bool valid = false, near = false, act = false;
                 if (lane < n) {
                     e = __ldg(&A.nbr[sb + lane]);
-                    active = entry_bucket(e.x) < L.b_stop;
+                    valid = QHP_IN_BOUNDS(entry_j(e.x), A.N, A.status);
+                    near = entry_bucket(e.x) < L.b_stop;
+                    act = valid && entry_bucket(e.x) < L.b_act;
+                    if (act && L.reach_i > 0.0f) {
+                        const float dx = __int_as_float(e.y), dy = __int_as_float(e.z), dz = __int_as_float(e.w);
+                        const float r = L.reach_i + sqrtf(__ldg(&A.dev_atom[entry_j(e.x)])) * 1.000001f;
+                        act = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < r * r;
+                    }
                 }
-                const unsigned am = __ballot_sync(0xffffffffu, active);
-                if (am == 0u) {
+                if (__ballot_sync(0xffffffffu, near) == 0u) {   // rows come in bucket order
                     beyond = true;
                     break;
                 }
-                const int nit = (__popc(am) + EPI - 1) / EPI;   // active entries form a prefix (bucket order)
-                float dx = 0.5f * c.L, dy = 0.5f * c.L, dz = 0.5f * c.L;
-                int jj = L.i;
-                if (lane < n && QHP_IN_BOUNDS(entry_j(e.x), A.N, A.status)) {
-                    dx = __int_as_float(e.y), dy = __int_as_float(e.z), dz = __int_as_float(e.w);
-                    jj = entry_j(e.x);
+                // Entries within reach first, in row order, then (skipping off) the others, which
+                // add exactly zero: the slots' summation order is the same either way.
+                const unsigned am = __ballot_sync(0xffffffffu, act);
+                const unsigned vm = __ballot_sync(0xffffffffu, valid);
+                const unsigned lt = (1u << lane) - 1u;
+                const int na = __popc(am);
+                const int cnt = A.skip ? na : __popc(vm);
+                int rank = -1;
+                if (act) rank = __popc(am & lt);
+                else if (!A.skip && valid) rank = na + __popc(vm & ~am & lt);
+                const int nit = (cnt + EPI - 1) / EPI;
+                __syncwarp();
+                if (rank >= 0) {
+                    const float dx = __int_as_float(e.y), dy = __int_as_float(e.z), dz = __int_as_float(e.w);
+                    ent[rank][0] = make_float4(dx, dx, dy, dy);
+                    ent[rank][1] = make_float4(dz, dz, __int_as_float(entry_j(e.x)), 0.0f);
+                }
+                if (lane >= cnt) {   // the last pass's spare slots: atom i itself, L/2 away
+                    const float h = 0.5f * c.L;
+                    ent[lane][0] = make_float4(h, h, h, h);
+                    ent[lane][1] = make_float4(h, h, __int_as_float(L.i), 0.0f);
                 }
                 __syncwarp();
-                ent[lane][0] = make_float4(dx, dx, dy, dy);
-                ent[lane][1] = make_float4(dz, dz, __int_as_float(jj), 0.0f);
-                __syncwarp();
+#ifdef QHP_PAIR_PIPE2
+                // two entries per lane in flight: both partners gathered before either is used
+                for (int it = 0; it < nit; it += 2) {
+                    const int i0 = it * EPI + L.slot, i1 = min(it + 1, nit - 1) * EPI + L.slot;
+                    const float4 a0 = ent[i0][0], b0 = ent[i0][1];
+                    const float4 a1 = ent[i1][0], b1 = ent[i1][1];
+                    float2 px0, py0, pz0, px1, py1, pz1;
+                    load_pair_beads<P>(pw, __float_as_int(b0.z), L.bp, px0, py0, pz0);
+                    load_pair_beads<P>(pw, __float_as_int(b1.z), L.bp, px1, py1, pz1);
+                    pair_entry_at<P, ALL, LJ, ENERGY>(make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                                                      make_float2(b0.x, b0.y), px0, py0, pz0, L.nxi, L.nyi, L.nzi, qq, c,
+                                                      fx, fy, fz, en);
+                    if (it + 1 < nit)
+                        pair_entry_at<P, ALL, LJ, ENERGY>(make_float2(a1.x, a1.y), make_float2(a1.z, a1.w),
+                                                          make_float2(b1.x, b1.y), px1, py1, pz1, L.nxi, L.nyi, L.nzi, qq,
+                                                          c, fx, fy, fz, en);
+                }
+#else
                 for (int it = 0; it < nit; ++it) {
                     const float4 a = ent[it * EPI + L.slot][0], b = ent[it * EPI + L.slot][1];
                     pair_entry<P, ALL, LJ, ENERGY>(make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
                                                    __float_as_int(b.z), pw, L.bp, L.nxi, L.nyi, L.nzi, qq, c, fx, fy, fz, en);
                 }
+#endif
             }
         }
         pair_block_sum<P>(fx, fy, fz, L.slot, L.bp, acc);
@@ -422,13 +464,21 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& s
         sm.acc[w][0][2 * bp] = sm.acc[w][1][2 * bp] = sm.acc[w][2][2 * bp] = 0;
         sm.acc[w][0][2 * bp + 1] = sm.acc[w][1][2 * bp + 1] = sm.acc[w][2][2 * bp + 1] = 0;
     }
-    // first bucket beyond reach of any bead pair (LIST_BUCKETS + 2: none is skipped)
-    L.b_stop = LIST_BUCKETS + 2;
+    // Reach: a bead pair of entry (i, j) lies at |D_ij + (x_jb - A_j) - (x_ib - A_i)| >=
+    // |D_ij| - dev_j - dev_i, so beyond rc + dev_i + dev_j no bead pair comes within rc and
+    // the entry adds exactly zero.  The row's bucket bound uses dev_i and the global maximum
+    // for dev_j (LIST_BUCKETS + 2: no bound); the per-entry test each partner's own dev_j.
+    L.b_stop = L.b_act = LIST_BUCKETS + 2;
+    L.reach_i = 0.0f;
     if (!ALL && A.dev_max) {
         const float m2 = __uint_as_float(*A.dev_max);
-        if (m2 >= 0.0f && m2 <= 1.0e4f) {
-            const float reach = c.rc + 2.0f * sqrtf(m2) * 1.000001f + 1.0e-3f;
-            L.b_stop = list_bucket_d2(reach * reach, c.bucket_lo, c.bucket_inv) + 1;   // above reach's own bucket
+        const float di2 = A.dev_atom ? A.dev_atom[i] : m2;
+        if (m2 >= 0.0f && m2 <= 1.0e4f && di2 >= 0.0f && di2 <= m2) {
+            const float ri = c.rc + sqrtf(di2) * 1.000001f + 1.0e-3f;
+            const float reach = ri + sqrtf(m2) * 1.000001f;
+            L.b_act = list_bucket_d2(reach * reach, c.bucket_lo, c.bucket_inv) + 1;   // above reach's own bucket
+            if (A.dev_atom) L.reach_i = ri;
+            if (A.skip) L.b_stop = L.b_act;
         }
     }
     const int ka = A.start[i];
@@ -493,8 +543,11 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& s
 // choice (48-62 registers, 8-10 blocks per SM) left the gathers' latency exposed; 12 blocks
 // (40 registers, a few spilled words) measured 5-10% faster at P = 32.  P <= 2 keep the
 // compiler's allocation.
+#ifndef QHP_PAIR_MIN_BLOCKS
+#define QHP_PAIR_MIN_BLOCKS 12
+#endif
 template <int P>
-__host__ __device__ constexpr int pair_min_blocks() { return P >= 4 ? 12 : 0; }
+__host__ __device__ constexpr int pair_min_blocks() { return P >= 4 ? QHP_PAIR_MIN_BLOCKS : 0; }
 
 template <int P, int W, bool ALL, bool ENERGY>
 __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_min_blocks<P>()) k_pair_mixed(const __grid_constant__ PairArgs A) {
@@ -983,7 +1036,9 @@ PairArgs make_pair_args(const qhp_system_s* s) {
     A.F = s->Ffix;
     A.epair = s->e_pair;
     A.status = s->status;
-    A.dev_max = s->pair_skip ? s->dev_max : nullptr;
+    A.dev_max = s->dev_max;
+    A.dev_atom = s->dev_atom;
+    A.skip = s->pair_skip;
     A.c = make_pair_consts(s);
     return A;
 }
@@ -1179,6 +1234,7 @@ cudaError_t launch_pair_contracted(qhp_system_s* s) {
     A.P = s->pc;
     A.W = s->pair_w > 0 ? s->pair_w : pair_warps_default(s->pc);
     A.pos = s->pos_c;
+    A.dev_atom = s->dev_atom_c;
     A.F = s->Ffix_s;
     switch (s->pc) {
         case 1: pair_mixed_dispatch<1>(A, false, s->stream); break;

@@ -34,6 +34,7 @@ struct IntegrateArgs {
     float4* pos_f4;
     double* pos_d;
     unsigned* dev_max;
+    float* dev_atom;       // mixed: per sorted atom, max over beads of |x_ib - A_i|^2 (or null)
     const float* qtb_u;
     float *qtb_v, *qtb_F;
     const int* gate;       // if set, the kernel runs only when *gate != 0
@@ -139,6 +140,8 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
     const bool valid = a < A.N;
     const int idx = (a * 3 + d) * P + n;
 
+    __shared__ unsigned dev_s[BLOCK / 3];   // per atom of the group: max squared bead deviation
+    if (t < A.apb) dev_s[t] = 0u;
     // transpose to [mode k][bead b] so that the lanes (beads) of a warp read consecutive words
     if (load_T)
         for (int e = t; e < P * P; e += BLOCK) {
@@ -212,8 +215,13 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
         const int base = la * 3 * P;
         const float x0 = xr[base + n], x1 = xr[base + P + n], x2 = xr[base + 2 * P + n];
         dv = x0 * x0 + x1 * x1 + x2 * x2;
+        if (A.dev_atom) atomicMax(&dev_s[la], __float_as_uint(dv));   // dv >= 0: float order == unsigned order
     }
-    block_max_atomic(dv, A.dev_max);
+    block_max_atomic(dv, A.dev_max);   // ends with a barrier
+    if (A.dev_atom && t < A.apb) {
+        const int a2 = bx * A.apb + t;
+        if (a2 < A.N && QHP_IN_BOUNDS(A.iperm[a2], A.N, A.status)) A.dev_atom[A.iperm[a2]] = __uint_as_float(dev_s[t]);
+    }
 }
 
 // Persistent grid: a block walks atom groups blockIdx.x, + gridDim.x, ... and stages the
@@ -443,9 +451,12 @@ __global__ void k_beads_fp64(int N, int P, const double* Q, const double* Tm, do
 __global__ void __launch_bounds__(128) k_contract(int N, int P, int Pc, const double* __restrict__ Q,
                                                   const float* __restrict__ Cf, const double* __restrict__ anchor,
                                                   const int* __restrict__ iperm, float4* __restrict__ pos_c,
-                                                  unsigned* dev_max, const int* gate) {
+                                                  unsigned* dev_max, float* dev_atom_c, const int* gate) {
     if (gate && !*gate) return;
+    __shared__ unsigned dev_s[128];   // per atom of the block (Pc divides 128): max squared deviation
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    dev_s[threadIdx.x] = 0u;
+    __syncthreads();
     float dv = 0.0f;
     if (t < N * Pc) {
         const int a = t / Pc, b = t % Pc;
@@ -464,6 +475,12 @@ __global__ void __launch_bounds__(128) k_contract(int N, int P, int Pc, const do
         float* pw = reinterpret_cast<float*>(pos_c);
         for (int d = 0; d < 3; ++d) pw[bead_word(iperm[a], b, d, Pc)] = x[d];
         dv = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        atomicMax(&dev_s[threadIdx.x / Pc], __float_as_uint(dv));
+    }
+    __syncthreads();
+    if (t < N * Pc && t % Pc == 0) {
+        const int a = t / Pc;
+        dev_atom_c[iperm[a]] = __uint_as_float(dev_s[threadIdx.x / Pc]);
     }
     for (int o = 16; o > 0; o >>= 1) dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, o));
     if ((threadIdx.x & 31) == 0) atomicMax(dev_max, __float_as_uint(dv));
@@ -607,6 +624,7 @@ static IntegrateArgs make_iargs(qhp_system_s* s) {
     A.pos_f4 = s->pos_f4;
     A.pos_d = s->pos_d;
     A.dev_max = s->dev_max;
+    A.dev_atom = s->dev_atom;
     A.status = s->status;
     A.qtb_u = s->qtb_u;
     A.qtb_v = s->qtb_v;
@@ -779,7 +797,8 @@ cudaError_t launch_contract(qhp_system_s* s, bool gated) {
     const int total = s->N * s->pc;
     s->launches++;
     k_contract<<<(total + 127) / 128, 128, 0, s->stream>>>(s->N, s->P, s->pc, s->Q, s->Cmat_f, s->anchor, s->iperm,
-                                                           s->pos_c, s->dev_max, gated ? s->rebuild_flag : nullptr);
+                                                           s->pos_c, s->dev_max, s->dev_atom_c,
+                                                           gated ? s->rebuild_flag : nullptr);
     return cudaGetLastError();
 }
 

@@ -255,6 +255,8 @@ struct qhp_system_s {
     unsigned* status_host = nullptr;                         // pinned copy, refreshed after each step call
     cudaEvent_t status_event = nullptr;
     unsigned* dev_max = nullptr;                             // max squared deviation (float bits)
+    float* dev_atom = nullptr;     // mixed: per sorted atom, max over beads of |x_ib - A_i|^2 this step
+    float* dev_atom_c = nullptr;   // the same over the contracted beads (RESPA)
     int* rebuild_flag = nullptr;
     unsigned long long* step_ctr = nullptr;                  // device copy of the step counter
     int64_t rebuilds_host = 0;
