@@ -523,7 +523,7 @@ def run_batch(args, ws, rank, local):
                          "peak_source": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} clock)"},
             "clocks": clk.summary(),
             "gpu_launches": int(i1.kernel_launches - i0.kernel_launches),
-            "stage_ms": dict(zip(["integrate_transform_check", "list_rebuild", "forces", "bonded (in forces)",
+            "stage_ms": dict(zip(["integrate_transform_check", "rebuild_bodies", "forces", "bonded (in forces)",
                                   "project_kick"], [round(float(x), 5) for x in st])),
             "list_rebuilds": int(i1.rebuilds - i0.rebuilds),
         }

@@ -270,16 +270,26 @@ int qhp_bar(const double* dU_A, int n_A, const double* dU_B, int n_B, double bet
 
 /* Batched systems (the paper's bead parallelism extended to many independent systems;
  * no counterpart in the paper).  A batch steps n_sys initialised mixed-precision systems
- * with the PILE or NVE thermostat together: each step is one CUDA graph of three batched
- * launches - integrate (with every system's list check, run by the block that finishes
- * the system), forces (pair items of every bead count, small-box path and warps-per-atom
- * setting and the bonded items of every system in one launch, added as int64 fixed point),
- * projection; persistent grids over (system, block) work items - plus one conditional
- * rebuild chain per system that runs only when that system's list check fires.
- * kernels_per_step counts the batched launches (3).  Results are bit-identical to stepping
- * every system alone.  In qhp_batch_info, grid_pair and items_pair describe the force
- * launch (grid_bonded is 0); in qhp_batch_get_profile, pair_ms is the force launch and
- * bonded_ms is 0.  The systems stay owned by the caller and must
+ * with the PILE or NVE thermostat (no RESPA) together: each step is one CUDA graph holding
+ * one cooperative launch over every system - integrate (with each system's list check, run
+ * by the block that finishes the system), forces (pair items of every bead count, small-box
+ * path and warps-per-atom setting and the bonded items, added as int64 fixed point),
+ * projection: three phases between grid barriers, persistent blocks over (system, group)
+ * work items - plus one conditional node per system that runs only when that system's list
+ * check fired: its list rebuild, forces and projection with the single-system kernels.
+ * kernels_per_step counts the batched launches (1).  Results are bit-identical to stepping
+ * every system alone.  In qhp_batch_info, grid_integrate and grid_project are the launch's
+ * blocks, grid_pair its half blocks (pair and bonded items; grid_bonded is 0) and items_pair
+ * its pair items; in qhp_batch_get_profile, integrate_ms, pair_ms (pair and bonded) and
+ * project_ms are the launch's phases from device clock stamps, list_ms the conditional
+ * bodies and bonded_ms 0.
+ *
+ * A grid barrier that waits longer than the batch's wait limit (default 2 s;
+ * qhp_batch_set_wait_limit, 1e3 .. 1e11 ns) gives up: the launch ends and the next
+ * qhp_batch_sync returns QHP_ERR_TIMEOUT (the members' state is then undefined).
+ * qhp_selftest_grid_barrier runs the barrier with one arrival that never comes, so that
+ * every wait runs out after wait_ns (1e3 .. 1e10): it returns QHP_ERR_TIMEOUT with the
+ * ST_TIMEOUT bit (4) in *status when the time limit works.  The systems stay owned by the caller and must
  * outlive the batch; while batched, their work runs on the batch's stream (member calls
  * such as qhp_get_modes stay valid and ordered), and qhp_set_stream must not be called
  * on them.  qhp_batch_step is asynchronous; qhp_batch_sync waits and reports the first
@@ -304,8 +314,10 @@ int qhp_batch_sync(qhp_batch batch);
 int qhp_batch_set_stream(qhp_batch batch, void* stream);
 int qhp_batch_autotune(qhp_batch batch, int reps, int* tuned);
 int qhp_batch_get_info(qhp_batch batch, qhp_batch_info* out);
+int qhp_batch_set_wait_limit(qhp_batch batch, long long wait_ns);
+int qhp_selftest_grid_barrier(long long wait_ns, unsigned* status);
 /* Stage durations of the last batched step (ms), as qhp_get_profile: integrate (with the
- * list checks), rebuild bodies, forces, projection.  Synchronises the batch's stream. */
+ * list checks), conditional bodies, forces, projection.  Synchronises the batch's stream. */
 int qhp_batch_get_profile(qhp_batch batch, qhp_profile* out);
 int qhp_autotune(qhp_sys sys, int reps, int* warps_per_atom);
 /* Fix the warps per atom of the mixed pair kernel (1, 2 or 4; 0 = the default for P:

@@ -1,19 +1,15 @@
 // Many independent systems stepped together (the paper's bead parallelism taken one level
 // further: systems of uneven size and bead count share every launch).
 //
-// One batched step is one CUDA graph of three launches plus the rebuild bodies:
-//   k_integrate_batch  B-A-O-A and bead positions of every system, bead forces cleared; the
-//                      block that finishes a system's last item runs its displacement check
-//                      and sets its conditional node
-//   n_sys IF nodes     each system's list rebuild chain, run only when its check fired
-//   k_force_batch      nonbonded and bonded forces of every system in one persistent launch
-//                      (each item selects its pair specialisation - bead count, small-box
-//                      path, warps per atom - or the bonded terms); int64 atomic adds
-//   k_project_batch    force projection and closing B
-// A persistent grid walks (system, block) items in system order; the host scheduler
-// cuts the item list into one contiguous range per resident block with about equal
-// estimated work (bead-pair work of the list rows for the pair items), so uneven systems
-// balance and a block keeps its system's transform in shared memory across items.
+// One batched step is one CUDA graph: one cooperative launch of k_step_batch over every
+// system (integrate with each system's list check, forces, projection: three phases between
+// grid barriers, persistent blocks walking (system, group) items), then one conditional node
+// per system that runs only when that system's check fired in this step: the list rebuild and
+// that system's forces and projection with the single-system kernels.  A block walks its item
+// ranges in system order; the host scheduler cuts the item lists into one contiguous range per
+// block (per half block for the forces, one specialisation after another) with about equal
+// estimated work, so uneven systems balance and a block keeps its system's transform in shared
+// memory across items.
 //
 // The autotuner times the pair kernel of one system per bead count with 1, 2 and 4 warps
 // per atom and keeps the fastest for every system with that bead count.
@@ -33,7 +29,11 @@ struct qhp_batch_s {
     qhp::CheckArgs* check_args = nullptr;   // device [n_sys]
     int* done = nullptr;                    // device [n_sys]: integrate items finished this step
     int* nitems = nullptr;                  // device [n_sys]: integrate items per system
+    qhp::StepBatchState* state = nullptr;   // device: grid barriers, timeout status, phase stamps
     int items_pair = 0;
+    int grid = 0;                           // co-resident blocks of the step kernel
+    size_t smem = 0;
+    long long wait_ns = 2000000000LL;       // a grid barrier gives up after this long
     cudaGraphExec_t exec = nullptr;
     std::vector<int4*> nbr_seen;            // list buffers the stages were built for
     std::vector<int> rowcap_seen;
@@ -42,7 +42,7 @@ struct qhp_batch_s {
     int64_t launches = 0;
     int kernels_per_step = 0;
     std::vector<int> kernels_per_rebuild;
-    cudaEvent_t ev[5] = {};                 // stage timestamps of the last replayed step
+    cudaEvent_t ev[3] = {};                 // step kernel start / end, rebuild bodies end
 };
 
 namespace qhp {
@@ -67,7 +67,7 @@ int stage_upload(BatchStage& st, const void* args, size_t args_bytes, const std:
     stage_free(st);
     st.smem = smem;
     const int n = (int)items.size();
-    grid = std::max(1, std::min(grid, n));
+    grid = std::max(1, grid);   // blocks past the items get empty ranges
     double total = 0.0;
     for (double c : cost) total += c;
     // contiguous ranges: block g starts where the running cost first reaches g/grid of the total
@@ -94,7 +94,7 @@ int stage_upload(BatchStage& st, const void* args, size_t args_bytes, const std:
 int stage_upload_phased(BatchStage& st, const void* args, size_t args_bytes, const std::vector<int2>& items,
                         const std::vector<double>& cost, const std::vector<int>& phase, int grid) {
     const int n = (int)items.size();
-    grid = std::max(1, std::min(grid, n));
+    grid = std::max(1, grid);   // blocks past the items get empty ranges
     int n_phase = 0;
     for (int p : phase) n_phase = std::max(n_phase, p + 1);
     // per phase, its items in order and the cut into `grid` chunks of about equal cost
@@ -154,9 +154,12 @@ std::vector<qhp_system_s*> members(qhp_batch_s* b) { return std::vector<qhp_syst
 
 int build_stages(qhp_batch_s* b) {
     const std::vector<qhp_system_s*> v = members(b);
-    TRY(batch_stage_integrate(v, b->integrate));
-    TRY(batch_stage_force(v, b->force, &b->items_pair));
-    TRY(batch_stage_project(v, b->project));
+    int maxP = 1;
+    for (qhp_system_s* s : v) maxP = std::max(maxP, s->P);
+    TRY(step_batch_config(maxP, &b->grid, &b->smem));
+    TRY(batch_stage_integrate(v, b->integrate, b->grid));
+    TRY(batch_stage_force(v, b->force, &b->items_pair, 2 * b->grid));
+    TRY(batch_stage_project(v, b->project, b->grid));
     b->nbr_seen.clear();
     b->rowcap_seen.clear();
     b->pairw_seen.clear();
@@ -192,9 +195,11 @@ int capture(qhp_batch_s* b) {
     if (!b->nitems) QHP_CUDA(cudaMalloc(&b->nitems, sizeof(int) * n));
     std::vector<int> ni(n);
     for (int k = 0; k < n; ++k) ni[k] = batch_integrate_items(b->sys[k]);
+    if (!b->state) QHP_CUDA(cudaMalloc(&b->state, sizeof(StepBatchState)));
     QHP_CUDA(cudaMemcpy(b->check_args, ca.data(), sizeof(CheckArgs) * n, cudaMemcpyHostToDevice));
     QHP_CUDA(cudaMemcpy(b->nitems, ni.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     QHP_CUDA(cudaMemset(b->done, 0, sizeof(int) * n));
+    QHP_CUDA(cudaMemset(b->state, 0, sizeof(StepBatchState)));
 
     cudaError_t e = cudaStreamBeginCaptureToGraph(b->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
@@ -202,17 +207,17 @@ int capture(qhp_batch_s* b) {
         return cuda_fail(e, "batch capture start");
     }
     int rc = QHP_OK;
-    int kernels = 0;
     b->kernels_per_rebuild.assign(n, 0);
     auto fail = [&](cudaError_t err, const char* what) {
         if (rc == QHP_OK && err != cudaSuccess) rc = cuda_fail(err, what);
     };
-    // event-record nodes between the stages: every replay timestamps them
+    // event-record nodes around the launch and the rebuild bodies: every replay timestamps them
     auto mark = [&](int k) { fail(cudaEventRecordWithFlags(b->ev[k], b->stream, cudaEventRecordExternal), "batch event"); };
     mark(0);
-    fail(launch_batch_integrate(b->integrate, b->check_args, b->done, b->nitems, b->stream), "batch integrate");
+    fail(launch_step_batch(b->integrate, b->force, b->project, b->check_args, b->done, b->nitems, b->state, b->wait_ns,
+                           b->grid, b->smem, b->stream),
+         "batched step launch");
     mark(1);
-    kernels += 1;
     std::vector<cudaGraphNode_t> conds(n);
     if (rc == QHP_OK) {
         cudaStreamCaptureStatus cs;
@@ -236,16 +241,22 @@ int capture(qhp_batch_s* b) {
             fail(cudaStreamBeginCaptureToGraph(b->aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
                  "batch body capture");
             if (rc != QHP_OK) break;
+            // the rebuilt system's step from its list check on, as stepping it alone does
             qhp_system_s* s = b->sys[k];
             cudaStream_t keep = s->stream;
+            const int prof = s->prof_on;
             s->stream = b->aux;
+            s->prof_on = 0;
             const int64_t before = s->launches;
             cudaError_t e1 = launch_rebuild(s);
             if (e1 == cudaSuccess) e1 = launch_integrate_gated(s);
             if (e1 == cudaSuccess) e1 = launch_cover_check(s);
+            if (e1 == cudaSuccess) e1 = launch_forces(s, false);
+            if (e1 == cudaSuccess) e1 = launch_project(s, true);
             b->kernels_per_rebuild[k] = (int)(s->launches - before);
             s->launches = before;
             s->stream = keep;
+            s->prof_on = prof;
             cudaGraph_t out = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(b->aux, &out);
             fail(e1, "batch rebuild chain");
@@ -257,11 +268,6 @@ int capture(qhp_batch_s* b) {
                  "batch join");
     }
     mark(2);
-    fail(launch_batch_force(b->force, b->stream), "batch forces");
-    mark(3);
-    fail(launch_batch_project(b->project, b->stream), "batch project");
-    mark(4);
-    kernels += 2;
     cudaGraph_t g2 = nullptr;
     e = cudaStreamEndCapture(b->stream, &g2);
     if (rc == QHP_OK && e != cudaSuccess) rc = cuda_fail(e, "batch capture end");
@@ -273,7 +279,7 @@ int capture(qhp_batch_s* b) {
         }
     }
     cudaGraphDestroy(g);
-    b->kernels_per_step = kernels;
+    b->kernels_per_step = 1;
     return rc;
 }
 
@@ -381,8 +387,8 @@ int qhp_create_batch(qhp_batch* out, int n_sys, const qhp_sys* systems) {
     for (int k = 0; k < n_sys; ++k) {
         qhp_system_s* s = systems[k];
         if (!s || !s->beads_set || s->precision != QHP_MIXED ||
-            (s->th.kind != QHP_THERMO_PILE && s->th.kind != QHP_THERMO_NVE)) {
-            set_error("qhp_create_batch: system %d must be initialised, mixed precision, PILE or NVE", k);
+            (s->th.kind != QHP_THERMO_PILE && s->th.kind != QHP_THERMO_NVE) || s->respa_n) {
+            set_error("qhp_create_batch: system %d must be initialised, mixed precision, PILE or NVE, without RESPA", k);
             return QHP_ERR_STATE;
         }
         for (int j = 0; j < k; ++j)
@@ -396,7 +402,7 @@ int qhp_create_batch(qhp_batch* out, int n_sys, const qhp_sys* systems) {
     int rc = QHP_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
-    for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
     if (e != cudaSuccess) rc = cuda_fail(e, "batch streams");
     b->stream = b->own_stream;
     // every member starts with valid forces and list; from now on its work is queued on
@@ -431,7 +437,8 @@ int qhp_destroy_batch(qhp_batch b) {
     cudaFree(b->check_args);
     cudaFree(b->done);
     cudaFree(b->nitems);
-    for (int k = 0; k < 5; ++k)
+    cudaFree(b->state);
+    for (int k = 0; k < 3; ++k)
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     if (b->aux) cudaStreamDestroy(b->aux);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
@@ -475,7 +482,29 @@ int qhp_batch_step(qhp_batch b, int n) {
 int qhp_batch_sync(qhp_batch b) {
     if (!b) return QHP_ERR_ARG;
     QHP_CUDA(cudaStreamSynchronize(b->stream));
+    if (b->state) {
+        unsigned st = 0;
+        QHP_CUDA(cudaMemcpy(&st, &b->state->status, sizeof st, cudaMemcpyDeviceToHost));
+        if (st & ST_TIMEOUT) {
+            // the barrier words may be mid-count: start the next step from a clean state
+            QHP_CUDA(cudaMemset(b->state, 0, sizeof(StepBatchState)));
+            set_error("qhp_batch_sync: a grid barrier of the batched step waited longer than %lld ns", b->wait_ns);
+            return QHP_ERR_TIMEOUT;
+        }
+    }
     for (qhp_system_s* s : b->sys) TRY(system_sync(s));
+    return QHP_OK;
+}
+
+int qhp_batch_set_wait_limit(qhp_batch b, long long wait_ns) {
+    if (!b || wait_ns < 1000 || wait_ns > 100000000000LL) {
+        set_error("qhp_batch_set_wait_limit: wait_ns must lie in [1e3, 1e11]");
+        return QHP_ERR_ARG;
+    }
+    if (wait_ns != b->wait_ns) {
+        b->wait_ns = wait_ns;
+        drop_graph(b);
+    }
     return QHP_OK;
 }
 
@@ -517,14 +546,19 @@ int qhp_batch_get_profile(qhp_batch b, qhp_profile* out) {
         return QHP_ERR_STATE;
     }
     QHP_CUDA(cudaStreamSynchronize(b->stream));
-    float t[4];
-    for (int k = 0; k < 4; ++k) QHP_CUDA(cudaEventElapsedTime(&t[k], b->ev[k], b->ev[k + 1]));
-    out->integrate_ms = t[0];
-    out->list_ms = t[1];
-    out->pair_ms = t[2];   // the merged force stage: pair and bonded items
+    // phases of the step kernel from its device clock stamps; the rebuild bodies by events
+    StepBatchState h;
+    QHP_CUDA(cudaMemcpy(&h, b->state, sizeof h, cudaMemcpyDeviceToHost));
+    float launch_ms = 0.0f, bodies_ms = 0.0f;
+    QHP_CUDA(cudaEventElapsedTime(&launch_ms, b->ev[0], b->ev[1]));
+    QHP_CUDA(cudaEventElapsedTime(&bodies_ms, b->ev[1], b->ev[2]));
+    auto span = [&](int a, int c) { return h.ts[c] > h.ts[a] ? (float)((double)(h.ts[c] - h.ts[a]) * 1e-6) : 0.0f; };
+    out->integrate_ms = span(0, 1);   // with the list checks
+    out->pair_ms = span(1, 2);        // pair and bonded items
     out->bonded_ms = 0.0f;
-    out->project_ms = t[3];
-    out->step_ms = t[0] + t[1] + t[2] + t[3];
+    out->project_ms = span(2, 3);
+    out->list_ms = bodies_ms;         // conditional bodies: rebuilds and the rebuilt systems' forces
+    out->step_ms = launch_ms + bodies_ms;
     return QHP_OK;
 }
 
@@ -536,7 +570,7 @@ int qhp_batch_get_info(qhp_batch b, qhp_batch_info* out) {
     out->steps = b->steps;
     out->kernels_per_step = b->kernels_per_step;
     out->grid_integrate = b->integrate.grid;
-    out->grid_pair = b->force.grid;   // pair and bonded items share the force launch
+    out->grid_pair = b->force.grid;   // half blocks of the step kernel: pair and bonded items
     out->grid_bonded = 0;
     out->grid_project = b->project.grid;
     out->items_pair = b->items_pair;

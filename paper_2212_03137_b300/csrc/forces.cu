@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "qhp_internal.cuh"
+#include "step_bodies.cuh"
 
 namespace qhp {
 
@@ -213,15 +214,17 @@ __device__ __forceinline__ void pair_entry1(float Dx, float Dy, float Dz, float4
 }
 
 // One list entry (anchor separation D) for the lane's two beads, the partner's beads given.
+// wrap: a bead pair may need another image than D's (small boxes; otherwise every |d_c| < L/2
+// and the minimum image changes nothing, so skipping it changes no bit).
 template <int P, bool ALL, bool LJ, bool ENERGY>
 __device__ __forceinline__ void pair_entry_at(float2 Dx, float2 Dy, float2 Dz, float2 px, float2 py, float2 pz,
                                               float2 nxi, float2 nyi, float2 nzi, float2 qq, const PairConsts& c,
-                                              float2& fx, float2& fy, float2& fz, float2& en) {
+                                              float2& fx, float2& fy, float2& fz, float2& en, bool wrap = true) {
     // d = D_ij + (x_jb - x_ib): anchor separation plus the two bead offsets
     float2 dx = add2(add2(px, nxi), Dx);
     float2 dy = add2(add2(py, nyi), Dy);
     float2 dz = add2(add2(pz, nzi), Dz);
-    if (ALL) {   // small boxes: minimum image per bead pair
+    if (ALL && wrap) {   // small boxes: minimum image per bead pair
         dx = fma2(f2(-c.L), make_float2(rintf(dx.x * c.invL), rintf(dx.y * c.invL)), dx);
         dy = fma2(f2(-c.L), make_float2(rintf(dy.x * c.invL), rintf(dy.y * c.invL)), dy);
         dz = fma2(f2(-c.L), make_float2(rintf(dz.x * c.invL), rintf(dz.y * c.invL)), dz);
@@ -233,10 +236,10 @@ __device__ __forceinline__ void pair_entry_at(float2 Dx, float2 Dy, float2 Dz, f
 template <int P, bool ALL, bool LJ, bool ENERGY>
 __device__ __forceinline__ void pair_entry(float2 Dx, float2 Dy, float2 Dz, int j, const float* __restrict__ pw,
                                            int bp, float2 nxi, float2 nyi, float2 nzi, float2 qq, const PairConsts& c,
-                                           float2& fx, float2& fy, float2& fz, float2& en) {
+                                           float2& fx, float2& fy, float2& fz, float2& en, bool wrap) {
     float2 px, py, pz;
     load_pair_beads<P>(pw, j, bp, px, py, pz);
-    pair_entry_at<P, ALL, LJ, ENERGY>(Dx, Dy, Dz, px, py, pz, nxi, nyi, nzi, qq, c, fx, fy, fz, en);
+    pair_entry_at<P, ALL, LJ, ENERGY>(Dx, Dy, Dz, px, py, pz, nxi, nyi, nzi, qq, c, fx, fy, fz, en, wrap);
 }
 
 // Entries per deterministic partial sum: 32, or for few beads as many as make eight entries
@@ -357,16 +360,18 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
             for (int sb = kb; sb < bend; sb += 32) {
                 const int n = min(32, bend - sb);
                 int4 e = make_int4(0, 0, 0, 0);
-                bool valid = false, near = false, act = false;
+                bool valid = false, near = false, act = false, wrap = true;
                 if (lane < n) {
                     e = __ldg(&A.nbr[sb + lane]);
                     valid = QHP_IN_BOUNDS(entry_j(e.x), A.N, A.status);
                     near = entry_bucket(e.x) < L.b_stop;
                     act = valid && entry_bucket(e.x) < L.b_act;
                     if (act && L.reach_i > 0.0f) {
+                        // e_ij = dev_i + dev_j (+ margin) bounds |(x_jb - A_j) - (x_ib - A_i)|
                         const float dx = __int_as_float(e.y), dy = __int_as_float(e.z), dz = __int_as_float(e.w);
                         const float r = L.reach_i + sqrtf(__ldg(&A.dev_atom[entry_j(e.x)])) * 1.000001f;
                         act = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < r * r;
+                        if (ALL) wrap = fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) + (r - c.rc) >= 0.499f * c.L;
                     }
                 }
                 if (__ballot_sync(0xffffffffu, near) == 0u) {   // rows come in bucket order
@@ -388,7 +393,7 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
                 if (rank >= 0) {
                     const float dx = __int_as_float(e.y), dy = __int_as_float(e.z), dz = __int_as_float(e.w);
                     ent[rank][0] = make_float4(dx, dx, dy, dy);
-                    ent[rank][1] = make_float4(dz, dz, __int_as_float(entry_j(e.x)), 0.0f);
+                    ent[rank][1] = make_float4(dz, dz, __int_as_float(entry_j(e.x)), wrap ? 1.0f : 0.0f);
                 }
                 if (lane >= cnt) {   // the last pass's spare slots: atom i itself, L/2 away
                     const float h = 0.5f * c.L;
@@ -396,30 +401,12 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
                     ent[lane][1] = make_float4(h, h, __int_as_float(L.i), 0.0f);
                 }
                 __syncwarp();
-#ifdef QHP_PAIR_PIPE2
-                // two entries per lane in flight: both partners gathered before either is used
-                for (int it = 0; it < nit; it += 2) {
-                    const int i0 = it * EPI + L.slot, i1 = min(it + 1, nit - 1) * EPI + L.slot;
-                    const float4 a0 = ent[i0][0], b0 = ent[i0][1];
-                    const float4 a1 = ent[i1][0], b1 = ent[i1][1];
-                    float2 px0, py0, pz0, px1, py1, pz1;
-                    load_pair_beads<P>(pw, __float_as_int(b0.z), L.bp, px0, py0, pz0);
-                    load_pair_beads<P>(pw, __float_as_int(b1.z), L.bp, px1, py1, pz1);
-                    pair_entry_at<P, ALL, LJ, ENERGY>(make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
-                                                      make_float2(b0.x, b0.y), px0, py0, pz0, L.nxi, L.nyi, L.nzi, qq, c,
-                                                      fx, fy, fz, en);
-                    if (it + 1 < nit)
-                        pair_entry_at<P, ALL, LJ, ENERGY>(make_float2(a1.x, a1.y), make_float2(a1.z, a1.w),
-                                                          make_float2(b1.x, b1.y), px1, py1, pz1, L.nxi, L.nyi, L.nzi, qq,
-                                                          c, fx, fy, fz, en);
-                }
-#else
                 for (int it = 0; it < nit; ++it) {
                     const float4 a = ent[it * EPI + L.slot][0], b = ent[it * EPI + L.slot][1];
                     pair_entry<P, ALL, LJ, ENERGY>(make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
-                                                   __float_as_int(b.z), pw, L.bp, L.nxi, L.nyi, L.nzi, qq, c, fx, fy, fz, en);
+                                                   __float_as_int(b.z), pw, L.bp, L.nxi, L.nyi, L.nzi, qq, c, fx, fy, fz, en,
+                                                   b.w != 0.0f);
                 }
-#endif
             }
         }
         pair_block_sum<P>(fx, fy, fz, L.slot, L.bp, acc);
@@ -437,15 +424,15 @@ __device__ __forceinline__ void pair_group(const PairArgs& A, const PairLane& L,
 // A block's FP32 sum is converted to int64 once and the integers are added, so the forces do
 // not depend on W.  Entries beyond rc + 2 max|x_ib - A_i| (+ margin) of every bead pair are
 // skipped (pair_group): they would add exactly zero.
-template <int P, int W, bool ALL, bool ENERGY, bool ACC = false>
-__device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& sm) {
+template <int P, int W, bool ALL, bool ENERGY, bool ACC = false, class Bar = BlockBar>
+__device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& sm, int tid) {
     constexpr bool ONE = P == 1;
     constexpr int LPE = ONE ? 1 : P / 2;
     constexpr int APB = PAIR_WARPS / W;
     constexpr int BLK = pair_block(P);
     const PairConsts& c = A.c;
     const float* __restrict__ pw = reinterpret_cast<const float*>(A.pos);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = tid & 31, w = tid >> 5;
     const int wa = w % W;
     const int i_raw = bx * APB + w / W;
     const bool live = i_raw < A.N;
@@ -470,7 +457,7 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& s
     // for dev_j (LIST_BUCKETS + 2: no bound); the per-entry test each partner's own dev_j.
     L.b_stop = L.b_act = LIST_BUCKETS + 2;
     L.reach_i = 0.0f;
-    if (!ALL && A.dev_max) {
+    if (A.dev_max) {   // |D| is the anchors' minimum image: the bound holds for every image
         const float m2 = __uint_as_float(*A.dev_max);
         const float di2 = A.dev_atom ? A.dev_atom[i] : m2;
         if (m2 >= 0.0f && m2 <= 1.0e4f && di2 >= 0.0f && di2 <= m2) {
@@ -503,7 +490,7 @@ __device__ __forceinline__ void pair_body(const PairArgs& A, int bx, PairSmem& s
             if (!ONE) sm.esum[w][2 * bp + 1] = en.y;
         }
     }
-    if (W > 1) __syncthreads();
+    if (W > 1) Bar::sync();
     else __syncwarp();
     // the first warp of each atom adds the W integer sums and writes each bead force once
     if (live && wa == 0 && slot == 0) {
@@ -552,7 +539,7 @@ __host__ __device__ constexpr int pair_min_blocks() { return P >= 4 ? QHP_PAIR_M
 template <int P, int W, bool ALL, bool ENERGY>
 __global__ void __launch_bounds__(32 * PAIR_WARPS, pair_min_blocks<P>()) k_pair_mixed(const __grid_constant__ PairArgs A) {
     __shared__ PairSmem sm;
-    pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, sm);
+    pair_body<P, W, ALL, ENERGY>(A, blockIdx.x, sm, threadIdx.x);
 }
 
 // FP64 path, small boxes: one warp per (sorted atom i, bead b), its lanes over i's list row,
@@ -827,11 +814,21 @@ __global__ void k_bonded(const __grid_constant__ BondArgs A) {
     bonded_body<MIXED, ENERGY>(A, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// Force stage of a batched step: one persistent launch over the items of every system - pair
-// items of every (bead count, small-box path, warps per atom) specialisation and bonded items -
-// in one grid.  Both add int64 fixed-point forces atomically into the forces the integrate
-// stage cleared: integer addition is exact, so the order of the items (and which block runs
-// which) cannot change a bit, and the sums equal a single system's store-then-add.
+// ------------------------------------------------------------------ one-launch batched step
+// A batched step over many systems in one cooperative launch of STEP_THREADS threads per block,
+// three phases separated by grid barriers:
+//   1. integrate: B-A-O-A and bead positions of every system's atom groups (threads 0..191);
+//      the block that finishes a system's last group runs its list check (batch_check);
+//   2. forces: the two 128-thread halves of each block walk their own ranges of pair items
+//      (every bead count, small-box path and warps-per-atom setting) and bonded items, adding
+//      int64 fixed-point forces atomically into the forces phase 1 cleared;
+//   3. projection and the closing B of every system (threads 0..191).
+// A system whose check fired skips phases 2 and 3 here: its conditional graph node rebuilds the
+// list and computes its forces and projection with the single-system kernels after the launch.
+// Integer addition is exact, so the order of the items (and which block runs which) cannot
+// change a bit: every member ends the step bit-identical to stepping it alone.
+constexpr int STEP_THREADS = 256;
+
 struct ForceArgs {
     PairArgs p;
     BondArgs b;
@@ -843,35 +840,155 @@ __host__ __device__ constexpr int batch_pair_stage(int lp, int all, int W) {
     return (lp * 2 + all) * 3 + (W == 4 ? 2 : W == 2 ? 1 : 0);
 }
 
-#define QHP_FORCE_CASE(LP, AL, WS)                                                                        \
-    case ((LP) * 2 + (AL)) * 3 + (WS):                                                                   \
-        pair_body<(1 << (LP)), ((WS) == 2 ? 4 : (WS) == 1 ? 2 : 1), ((AL) != 0), false, true>(A.p, bx, sm); \
+// Barriers of the step's sub-blocks: the 192 threads of the integrate / project groups, and
+// the two 128-thread halves of the force phase (named barriers 1, 2 and 3; 0 is the block's).
+struct GroupBar {
+    __device__ __forceinline__ static void sync() { asm volatile("bar.sync 1, 192;" ::: "memory"); }
+};
+struct HalfBar {
+    __device__ __forceinline__ static void sync() {
+        asm volatile("bar.sync %0, 128;" ::"r"(2 + (int)(threadIdx.x >> 7)) : "memory");
+    }
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier for a co-resident grid: every block's thread 0 reads the generation, counts
+// itself in and waits for the generation to move; the expected-th arrival resets the count,
+// stamps the phase and moves the generation.  A wait longer than wait_ns gives up: it sets
+// ST_TIMEOUT and the block leaves the step (so do the others when they see the bit), so a lost
+// block ends the launch with an error instead of a hang.  Returns false when the step ends.
+__device__ bool grid_sync(StepBatchState* st, unsigned expected, long long wait_ns, int stamp) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = &st->bar[1];
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&st->bar[0], 1u) == expected - 1u) {
+            atomicExch(&st->bar[0], 0u);
+            if (stamp >= 0) st->ts[stamp] = global_ns();
+            __threadfence();
+            atomicAdd(&st->bar[1], 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if ((long long)(global_ns() - t0) > wait_ns) {
+                    atomicOr(&st->status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile unsigned*)&st->status & ST_TIMEOUT) ok = 0;
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+struct StepBatchArgs {
+    const IntegrateArgs* iargs;
+    const int2* iitems;
+    const int* iranges;   // per block
+    const ForceArgs* fargs;
+    const int2* fitems;
+    const int* franges;   // per half block
+    const ProjectArgs* pargs;
+    const int2* pitems;
+    const int* pranges;   // per block
+    const CheckArgs* checks;
+    int* done;            // integrate items finished per system (reset by the last one)
+    const int* nitems;    // integrate items per system
+    StepBatchState* st;
+    long long wait_ns;
+};
+
+#define QHP_FORCE_CASE(LP, AL, WS)                                                                          \
+    case ((LP) * 2 + (AL)) * 3 + (WS):                                                                     \
+        pair_body<(1 << (LP)), ((WS) == 2 ? 4 : (WS) == 1 ? 2 : 1), ((AL) != 0), false, true, HalfBar>(A.p, bx, \
+                                                                                                      sm, lt); \
         break;
 #define QHP_FORCE_CASES_W(LP, AL) QHP_FORCE_CASE(LP, AL, 0) QHP_FORCE_CASE(LP, AL, 1) QHP_FORCE_CASE(LP, AL, 2)
 #define QHP_FORCE_CASES_P(LP) QHP_FORCE_CASES_W(LP, 0) QHP_FORCE_CASES_W(LP, 1)
-
-// 8 resident blocks (64 registers): the 42 inlined specialisations and the per-item arguments,
-// read from global memory rather than the parameter bank, spill heavily at 12 blocks (40).
-#ifndef QHP_FORCE_BATCH_MIN_BLOCKS
-#define QHP_FORCE_BATCH_MIN_BLOCKS 8
+// 4 resident blocks of 256 threads (64 registers): the 42 inlined pair specialisations and the
+// per-item arguments, read from global memory rather than the parameter bank, spill heavily at
+// 40 registers.
+#ifndef QHP_STEP_MIN_BLOCKS
+#define QHP_STEP_MIN_BLOCKS 4
 #endif
-__global__ void __launch_bounds__(32 * PAIR_WARPS, QHP_FORCE_BATCH_MIN_BLOCKS) k_force_batch(const ForceArgs* __restrict__ args,
-                                                                   const int2* __restrict__ items,
-                                                                   const int* __restrict__ ranges) {
-    __shared__ PairSmem sm;
-    for (int it = ranges[blockIdx.x]; it < ranges[blockIdx.x + 1]; ++it) {
-        const int2 w = items[it];
-        const int sys = w.x & 0xffff, kind = w.x >> 16, bx = w.y;
-        const ForceArgs& A = args[sys];
-        __syncthreads();   // the previous item's sums have been read
-        if (kind == FORCE_BONDED_VARIANT) {
-            bonded_body<true, false, true>(A.b, bx * (int)blockDim.x + threadIdx.x);
-            continue;
+__global__ void __launch_bounds__(STEP_THREADS, QHP_STEP_MIN_BLOCKS) k_step_batch(const __grid_constant__ StepBatchArgs S) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const unsigned nblk = gridDim.x;
+    if (blockIdx.x == 0 && tid == 0) S.st->ts[0] = global_ns();
+    // phase 1: integrate, and each system's list check by the block finishing its last group
+    if (tid < BLOCK) {
+        int prev = -1;
+        for (int it = S.iranges[blockIdx.x]; it < S.iranges[blockIdx.x + 1]; ++it) {
+            const int2 w = S.iitems[it];
+            GroupBar::sync();   // the previous group is done with shared memory
+            integrate_body<true, false, true, GroupBar>(S.iargs[w.x], w.y, smem_raw, w.x != prev);
+            prev = w.x;
+            GroupBar::sync();   // every thread of the group has written its modes, positions and forces
+            if (tid == 0) {
+                __threadfence();
+                if (atomicAdd(&S.done[w.x], 1) == S.nitems[w.x] - 1) {
+                    __threadfence();
+                    batch_check(S.checks[w.x]);
+                    S.done[w.x] = 0;   // for the next step
+                }
+            }
         }
-        switch (kind) {
-            QHP_FORCE_CASES_P(0) QHP_FORCE_CASES_P(1) QHP_FORCE_CASES_P(2) QHP_FORCE_CASES_P(3)
-            QHP_FORCE_CASES_P(4) QHP_FORCE_CASES_P(5) QHP_FORCE_CASES_P(6)
-            default: break;
+    }
+    if (!grid_sync(S.st, nblk, S.wait_ns, 1)) return;
+    // phase 2: forces, one item at a time per 128-thread half
+    {
+        const int h = tid >> 7, lt = tid & 127;
+        PairSmem& sm = reinterpret_cast<PairSmem*>(smem_raw)[h];
+        const int v = (int)blockIdx.x * 2 + h;
+        for (int it = S.franges[v]; it < S.franges[v + 1]; ++it) {
+            const int2 w = S.fitems[it];
+            const int sys = w.x & 0xffff, kind = w.x >> 16, bx = w.y;
+            HalfBar::sync();   // the previous item's sums have been read
+            if (*S.checks[sys].flag) continue;   // rebuilt this step: computed after the launch
+            const ForceArgs& A = S.fargs[sys];
+            if (kind == FORCE_BONDED_VARIANT) {
+                bonded_body<true, false, true>(A.b, bx * 128 + lt);
+                continue;
+            }
+            switch (kind) {
+                QHP_FORCE_CASES_P(0) QHP_FORCE_CASES_P(1) QHP_FORCE_CASES_P(2) QHP_FORCE_CASES_P(3)
+                QHP_FORCE_CASES_P(4) QHP_FORCE_CASES_P(5) QHP_FORCE_CASES_P(6)
+                default: break;
+            }
+        }
+    }
+    if (!grid_sync(S.st, nblk, S.wait_ns, 2)) return;
+    // phase 3: projection and the closing B
+    if (tid < BLOCK) {
+        int prev = -1;
+        for (int it = S.pranges[blockIdx.x]; it < S.pranges[blockIdx.x + 1]; ++it) {
+            const int2 w = S.pitems[it];
+            if (*S.checks[w.x].flag) continue;
+            GroupBar::sync();
+            project_body<true, true, GroupBar>(S.pargs[w.x], w.y, smem_raw, w.x != prev);
+            prev = w.x;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&S.st->bar[2], 1u) == nblk - 1u) {
+            S.st->ts[3] = global_ns();
+            S.st->bar[2] = 0u;
         }
     }
 }
@@ -879,6 +996,11 @@ __global__ void __launch_bounds__(32 * PAIR_WARPS, QHP_FORCE_BATCH_MIN_BLOCKS) k
 #undef QHP_FORCE_CASES_W
 #undef QHP_FORCE_CASES_P
 
+// Self-test of the barrier's time limit: the blocks wait for one arrival more than the grid
+// has, so every wait runs out after wait_ns and sets ST_TIMEOUT.
+__global__ void k_grid_sync_selftest(StepBatchState* st, long long wait_ns) {
+    grid_sync(st, gridDim.x + 1u, wait_ns, -1);
+}
 // Count in-cutoff bead pairs j > i (lane = bead, one list entry at a time); not on the step path.
 __global__ void k_count_pairs(int N, int P, int mixed, int all, const float4* __restrict__ pos_f,
                               const double* __restrict__ pos_d, const int* __restrict__ start,
@@ -1144,7 +1266,7 @@ cudaError_t launch_bonded(qhp_system_s* s, bool energy) {
 // costed by the warp passes of their list rows (a pass evaluates 32 / max(1, P/2) entries);
 // bonded items are blocks of 128 (molecule, bead) pairs.  Every resident block gets an equal
 // share of every specialisation's items, specialisation by specialisation.
-int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* n_pair_items) {
+int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* n_pair_items, int halves) {
     if (v.size() > 0xffff) {
         set_error("a batch holds at most 65535 systems");
         return QHP_ERR_ARG;
@@ -1182,13 +1304,8 @@ int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* 
         *n_pair_items = 0;
         for (const int2& w : items) *n_pair_items += (w.x >> 16) != FORCE_BONDED_VARIANT;
     }
-    int per_sm = 0;
-    QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_batch, 32 * PAIR_WARPS, 0));
     st.smem = 0;
-    const int grid = std::max(1, per_sm) * sm_count();
-#ifdef QHP_FORCE_BATCH_FLAT
-    return stage_upload(st, a.data(), sizeof(ForceArgs) * a.size(), items, cost, grid);
-#else
+    const int grid = halves;
     // one phase per specialisation present (in kind order, bonded last): the blocks of an SM run
     // the same code at about the same time instead of a mix of the 43 bodies
     std::vector<int> kinds;
@@ -1200,12 +1317,54 @@ int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* 
     for (size_t i = 0; i < items.size(); ++i)
         phase[i] = (int)(std::lower_bound(uniq.begin(), uniq.end(), kinds[i]) - uniq.begin());
     return stage_upload_phased(st, a.data(), sizeof(ForceArgs) * a.size(), items, cost, phase, grid);
-#endif
 }
 
-cudaError_t launch_batch_force(const BatchStage& st, cudaStream_t stream) {
-    k_force_batch<<<st.grid, 32 * PAIR_WARPS, 0, stream>>>((const ForceArgs*)st.args, st.items, st.ranges);
-    return cudaGetLastError();
+// Shared memory of the step kernel (the larger of the integrate / project group's and the two
+// halves' pair sums) and its co-resident grid: every block must be resident at once for the
+// grid barriers, which a cooperative launch of at most this many blocks guarantees.
+int step_batch_config(int maxP, int* grid, size_t* smem) {
+    const size_t sm = std::max(batch_group_smem(maxP), 2 * sizeof(PairSmem));
+    if (sm > 48 * 1024) QHP_CUDA(cudaFuncSetAttribute(k_step_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    QHP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch, STEP_THREADS, sm));
+    if (per_sm < 1) {
+        set_error("the batched step kernel does not fit on an SM");
+        return QHP_ERR_STATE;
+    }
+    *grid = per_sm * sm_count();
+    *smem = sm;
+    return QHP_OK;
+}
+
+cudaError_t launch_step_batch(const BatchStage& integ, const BatchStage& force, const BatchStage& proj,
+                              const CheckArgs* checks, int* done, const int* nitems, StepBatchState* state,
+                              long long wait_ns, int grid, size_t smem, cudaStream_t stream) {
+    StepBatchArgs S;
+    S.iargs = (const IntegrateArgs*)integ.args;
+    S.iitems = integ.items;
+    S.iranges = integ.ranges;
+    S.fargs = (const ForceArgs*)force.args;
+    S.fitems = force.items;
+    S.franges = force.ranges;
+    S.pargs = (const ProjectArgs*)proj.args;
+    S.pitems = proj.items;
+    S.pranges = proj.ranges;
+    S.checks = checks;
+    S.done = done;
+    S.nitems = nitems;
+    S.st = state;
+    S.wait_ns = wait_ns;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(STEP_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_batch, S);
 }
 
 cudaError_t launch_forces(qhp_system_s* s, bool energy) {
@@ -1261,3 +1420,30 @@ cudaError_t launch_count_pairs(qhp_system_s* s, unsigned long long* out2) {
 }
 
 }  // namespace qhp
+
+using namespace qhp;
+
+extern "C" int qhp_selftest_grid_barrier(long long wait_ns, unsigned* status_out) {
+    if (wait_ns < 1000 || wait_ns > 10000000000LL) {
+        set_error("qhp_selftest_grid_barrier: wait_ns must lie in [1e3, 1e10]");
+        return QHP_ERR_ARG;
+    }
+    StepBatchState* st = nullptr;
+    QHP_CUDA(cudaMalloc(&st, sizeof(StepBatchState)));
+    cudaError_t e = cudaMemset(st, 0, sizeof(StepBatchState));
+    if (e == cudaSuccess) {
+        void* args[] = {&st, &wait_ns};
+        e = cudaLaunchCooperativeKernel((const void*)k_grid_sync_selftest, dim3(2), dim3(32), args, 0, nullptr);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    StepBatchState h = {};
+    if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(st);
+    if (e != cudaSuccess) return cuda_fail(e, "grid barrier self-test");
+    if (status_out) *status_out = h.status;
+    if (h.status & ST_TIMEOUT) {
+        set_error("grid barrier wait ran out after %lld ns (self-test: one arrival never comes)", wait_ns);
+        return QHP_ERR_TIMEOUT;
+    }
+    return QHP_OK;
+}

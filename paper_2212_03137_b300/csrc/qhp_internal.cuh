@@ -416,11 +416,17 @@ int stage_upload_phased(BatchStage& st, const void* args, size_t args_bytes, con
                         const std::vector<double>& cost, const std::vector<int>& phase, int grid);
 void stage_free(BatchStage& st);
 int sm_count();
-int batch_stage_integrate(const std::vector<qhp_system_s*>& v, BatchStage& st);
-int batch_stage_project(const std::vector<qhp_system_s*>& v, BatchStage& st);
-constexpr int BATCH_PAIR_STAGES = 7 * 2 * 3;   // (log2 P, small-box path, W = 1, 2, 4)
-// Per-system record of the batched list check (the single-system k_check), run at the end of
-// the batched integrate stage by the block that completes the system's last item.
+// The one-launch batched step (k_step_batch): integrate and project items per block of the
+// step's grid, force items per half block (two halves of 128 threads).
+int batch_stage_integrate(const std::vector<qhp_system_s*>& v, BatchStage& st, int grid);
+int batch_stage_project(const std::vector<qhp_system_s*>& v, BatchStage& st, int grid);
+int batch_integrate_items(const qhp_system_s* s);   // atom groups of 64/P atoms
+size_t batch_group_smem(int maxP);                  // integrate / project shared memory
+constexpr int BATCH_PAIR_STAGES = 7 * 2 * 3;        // (log2 P, small-box path, W = 1, 2, 4)
+constexpr int FORCE_BONDED_VARIANT = BATCH_PAIR_STAGES;   // item kind of the batched bonded terms
+int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* n_pair_items, int halves);
+// Per-system record of the batched list check (the single-system k_check), run by the block
+// that completes the system's last integrate item.
 struct CheckArgs {
     unsigned* dev_max;
     int* flag;
@@ -428,13 +434,17 @@ struct CheckArgs {
     cudaGraphConditionalHandle cond;
     float thr2;
 };
-cudaError_t launch_batch_integrate(const BatchStage& st, const CheckArgs* checks, int* done, const int* nitems,
-                                   cudaStream_t stream);
-int batch_integrate_items(const qhp_system_s* s);
-constexpr int FORCE_BONDED_VARIANT = BATCH_PAIR_STAGES;   // item kind of the batched bonded terms
-int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* n_pair_items);
-cudaError_t launch_batch_force(const BatchStage& st, cudaStream_t stream);
-cudaError_t launch_batch_project(const BatchStage& st, cudaStream_t stream);
+// Device state of the step's grid barriers: [0] arrivals, [1] generation, [2] finished blocks.
+struct StepBatchState {
+    unsigned bar[4];
+    unsigned status;               // ST_TIMEOUT when a barrier wait ran out
+    unsigned pad;
+    unsigned long long ts[4];      // phase boundaries (globaltimer, ns) of the last step
+};
+int step_batch_config(int maxP, int* grid, size_t* smem);   // co-resident grid and shared memory
+cudaError_t launch_step_batch(const BatchStage& integ, const BatchStage& force, const BatchStage& proj,
+                              const CheckArgs* checks, int* done, const int* nitems, StepBatchState* state,
+                              long long wait_ns, int grid, size_t smem, cudaStream_t stream);
 
 int compute_energy(qhp_system_s* s, qhp_energy* out);
 int beads_fp64(qhp_system_s* s, double* dev_out);

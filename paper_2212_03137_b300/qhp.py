@@ -102,6 +102,8 @@ _SIGS = {
     "qhp_batch_autotune": [_VP, C.c_int, _IP],
     "qhp_batch_get_info": [_VP, _VP],
     "qhp_batch_get_profile": [_VP, _VP],
+    "qhp_batch_set_wait_limit": [_VP, C.c_longlong],
+    "qhp_selftest_grid_barrier": [C.c_longlong, C.POINTER(C.c_uint)],
     "qhp_autotune": [_VP, C.c_int, _IP],
     "qhp_set_pair_warps": [_VP, C.c_int],
     "qhp_set_pair_skip": [_VP, C.c_int],
@@ -415,6 +417,17 @@ def qhp_batch_get_profile(b):
     p = qhp_profile()
     _check(lib().qhp_batch_get_profile(b, C.cast(C.byref(p), C.c_void_p)))
     return p
+
+
+def qhp_batch_set_wait_limit(b, wait_ns: int) -> None:
+    _check(lib().qhp_batch_set_wait_limit(b, int(wait_ns)))
+
+
+def qhp_selftest_grid_barrier(wait_ns: int) -> tuple[int, int]:
+    """(return code, status word) of the grid barrier's time-limit self-test; not raised."""
+    st = C.c_uint(0)
+    rc = lib().qhp_selftest_grid_barrier(int(wait_ns), C.byref(st))
+    return rc, st.value
 
 
 def qhp_autotune(h, reps: int = 5) -> int:

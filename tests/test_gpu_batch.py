@@ -1,7 +1,9 @@
 """Batched systems: many uneven boxes stepped by the batched launches give, bit for bit,
-the trajectories of the same boxes stepped one at a time (the force stage adds every
-system's pair and bonded terms as int64 atomics in one launch; integer sums do not depend
-on their order), and those match the FP64 oracle at the mixed-precision tolerance."""
+the trajectories of the same boxes stepped one at a time (one cooperative launch per step
+adds every system's pair and bonded terms as int64 atomics; integer sums do not depend on
+their order; a system whose list check fires finishes its step in a conditional node with
+the single-system kernels), and those match the FP64 oracle at the mixed-precision
+tolerance."""
 import numpy as np
 import pytest
 
@@ -44,9 +46,9 @@ def test_batch_equals_single_systems_bitwise():
         b.step(15)
         b.sync()
         info = qhp.qhp_batch_get_info(b.h)
-        # three launches whatever the mix: integrate + checks, every system's forces, projection
-        assert info.n_sys == len(MIX) and info.steps == 25 and info.kernels_per_step == 3
-        assert info.grid_bonded == 0 and info.items_pair > 0 and info.grid_pair > 0
+        # one cooperative launch whatever the mix (integrate + checks, forces, projection)
+        assert info.n_sys == len(MIX) and info.steps == 25 and info.kernels_per_step == 1
+        assert info.grid_bonded == 0 and info.items_pair > 0 and info.grid_pair == 2 * info.grid_integrate
         assert info.atom_beads == sum(3 * c.n_mol * c.P for c in MIX)
         for s, m in zip(singles, members):
             Qa, Pa = qhp.qhp_get_modes(s.h)

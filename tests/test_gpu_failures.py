@@ -7,6 +7,10 @@ the CUDA context stays usable: a fresh system steps normally afterwards.  The fa
 made by the caller's inputs: a NaN in a normal mode, a bead pushed outside the skin, and a
 time step far beyond the O-H stretch's stability limit.  The 64-water box runs without a cell
 grid, and no index is ever formed from a position.
+
+The batched step's grid barriers wait with a time limit: the self-test runs the barrier with
+one arrival that never comes (a count that nothing completes), every wait gives up after the
+limit with ST_TIMEOUT, and the context stays usable.
 """
 import math
 
@@ -76,3 +80,27 @@ def test_absurd_time_step_is_reported():
                 qhp.qhp_sync(s.h)
         assert e.value.code in REPORTED
     _healthy("mixed")
+
+
+def test_grid_barrier_wait_runs_out_and_reports_timeout():
+    """20 ms limit, one missing arrival: QHP_ERR_TIMEOUT with ST_TIMEOUT, in well under a second."""
+    import time
+    t0 = time.perf_counter()
+    rc, status = qhp.qhp_selftest_grid_barrier(20_000_000)
+    elapsed = time.perf_counter() - t0
+    assert rc == -3 and status & 4, (rc, status)
+    assert elapsed < 5.0
+    _healthy("mixed")
+
+
+def test_batch_wait_limit_is_validated_and_steps_run_under_it():
+    from paper_2212_03137_b300.workloads import small_mixed_config
+    systems = [qhp.System.from_config(small_mixed_config(n, P=p, seed=n)) for n, p in ((64, 4), (216, 8))]
+    with qhp.Batch(systems) as b:
+        with pytest.raises(qhp.QHPError):
+            qhp.qhp_batch_set_wait_limit(b.h, 10)
+        qhp.qhp_batch_set_wait_limit(b.h, 500_000_000)
+        b.step(5)
+        b.sync()
+    for s in systems:
+        s.close()
