@@ -106,8 +106,7 @@ typedef struct {
     int n_atoms, P, precision, list_mode; /* list_mode 1: centroid Verlet list, 0: all pairs */
     int64_t step, rebuilds, list_entries, list_capacity;
     int64_t kernel_launches;              /* kernels this system has launched so far */
-    int n_cells_per_edge;
-    int early_rebuilds;                   /* of rebuilds, those run at the end of a step */
+    int n_cells_per_edge, reserved;
 } qhp_info;
 
 /* Create a system of n_atoms atoms in a cubic periodic box of edge box_L (A): the

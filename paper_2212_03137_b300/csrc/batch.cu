@@ -3,11 +3,9 @@
 //
 // One batched step is one CUDA graph: one cooperative launch of k_step_batch over every
 // system (integrate with each system's list check, forces, projection: three phases between
-// grid barriers, persistent blocks walking (system, group) items), then two conditional nodes
-// per system.  The check's usual outcome is the end-of-step rebuild (the deviation maximum
-// would pass skin/2 within two steps): its node rebuilds the list for the next step.  When a
-// bead is already past skin/2 the other node rebuilds the list and finishes that system's
-// step (forces, projection) with the single-system kernels.  A block walks its item
+// grid barriers, persistent blocks walking (system, group) items), then one conditional node
+// per system that runs only when that system's check fired in this step: the list rebuild and
+// that system's forces and projection with the single-system kernels.  A block walks its item
 // ranges in system order; the host scheduler cuts the item lists into one contiguous range per
 // block (per half block for the forces, one specialisation after another) with about equal
 // estimated work, so uneven systems balance and a block keeps its system's transform in shared
@@ -43,7 +41,7 @@ struct qhp_batch_s {
     int64_t steps = 0;
     int64_t launches = 0;
     int kernels_per_step = 0;
-    std::vector<int> kernels_per_rebuild, kernels_per_early;
+    std::vector<int> kernels_per_rebuild;
     cudaEvent_t ev[3] = {};                 // step kernel start / end, rebuild bodies end
 };
 
@@ -180,18 +178,17 @@ int capture(qhp_batch_s* b) {
     const int n = (int)b->sys.size();
     cudaGraph_t g = nullptr;
     QHP_CUDA(cudaGraphCreate(&g, 0));
-    std::vector<cudaGraphConditionalHandle> handles(2 * n);   // [2k] rebuild now, [2k + 1] at the end of the step
+    std::vector<cudaGraphConditionalHandle> handles(n);
     std::vector<CheckArgs> ca(n);
     for (int k = 0; k < n; ++k) {
         qhp_system_s* s = b->sys[k];
-        cudaError_t e = cudaGraphConditionalHandleCreate(&handles[2 * k], g, 0, cudaGraphCondAssignDefault);
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handles[2 * k + 1], g, 0, cudaGraphCondAssignDefault);
+        cudaError_t e = cudaGraphConditionalHandleCreate(&handles[k], g, 0, cudaGraphCondAssignDefault);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
             return cuda_fail(e, "batch conditional handle");
         }
-        ca[k] = CheckArgs{s->dev_max, s->dev_prev, s->rebuild_flag, s->rebuild_count, handles[2 * k],
-                          handles[2 * k + 1], (float)(0.5 * s->ff.skin)};
+        const float half = (float)(0.5 * s->ff.skin);
+        ca[k] = CheckArgs{s->dev_max, s->rebuild_flag, s->rebuild_count, handles[k], half * half};
     }
     if (!b->check_args) QHP_CUDA(cudaMalloc(&b->check_args, sizeof(CheckArgs) * n));
     if (!b->done) QHP_CUDA(cudaMalloc(&b->done, sizeof(int) * n));
@@ -211,7 +208,6 @@ int capture(qhp_batch_s* b) {
     }
     int rc = QHP_OK;
     b->kernels_per_rebuild.assign(n, 0);
-    b->kernels_per_early.assign(n, 0);
     auto fail = [&](cudaError_t err, const char* what) {
         if (rc == QHP_OK && err != cudaSuccess) rc = cuda_fail(err, what);
     };
@@ -222,7 +218,7 @@ int capture(qhp_batch_s* b) {
                            b->grid, b->smem, b->stream),
          "batched step launch");
     mark(1);
-    std::vector<cudaGraphNode_t> conds(2 * n);
+    std::vector<cudaGraphNode_t> conds(n);
     if (rc == QHP_OK) {
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg = nullptr;
@@ -231,41 +227,33 @@ int capture(qhp_batch_s* b) {
         size_t nd = 0;
         fail(cudaStreamGetCaptureInfo(b->stream, &cs, nullptr, &cg, &deps, &ed, &nd), "batch capture info");
         std::vector<cudaGraphNode_t> dep(deps, deps + nd);
-        for (int c = 0; c < 2 * n && rc == QHP_OK; ++c) {
-            const int k = c / 2;
-            const bool early = (c & 1) != 0;
+        for (int k = 0; k < n && rc == QHP_OK; ++k) {
             alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
             memset(pbuf, 0, sizeof pbuf);
             cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(pbuf);
             p.type = cudaGraphNodeTypeConditional;
-            p.conditional.handle = handles[c];
+            p.conditional.handle = handles[k];
             p.conditional.type = cudaGraphCondTypeIf;
             p.conditional.size = 1;
-            fail(cudaGraphAddNode(&conds[c], cg, dep.data(), nullptr, dep.size(), &p), "batch conditional node");
+            fail(cudaGraphAddNode(&conds[k], cg, dep.data(), nullptr, dep.size(), &p), "batch conditional node");
             if (rc != QHP_OK) break;
             cudaGraph_t body = p.conditional.phGraph_out[0];
             fail(cudaStreamBeginCaptureToGraph(b->aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
                  "batch body capture");
             if (rc != QHP_OK) break;
-            // rebuild now: the system's step from its list check on, as stepping it alone does;
-            // end of step: the list for the next step from the current centroids
+            // the rebuilt system's step from its list check on, as stepping it alone does
             qhp_system_s* s = b->sys[k];
             cudaStream_t keep = s->stream;
             const int prof = s->prof_on;
             s->stream = b->aux;
             s->prof_on = 0;
             const int64_t before = s->launches;
-            cudaError_t e1 = cudaSuccess;
-            if (early) {
-                e1 = launch_early_rebuild(s);
-            } else {
-                e1 = launch_rebuild(s);
-                if (e1 == cudaSuccess) e1 = launch_integrate_gated(s);
-                if (e1 == cudaSuccess) e1 = launch_cover_check(s);
-                if (e1 == cudaSuccess) e1 = launch_forces(s, false);
-                if (e1 == cudaSuccess) e1 = launch_project(s, true);
-            }
-            (early ? b->kernels_per_early : b->kernels_per_rebuild)[k] = (int)(s->launches - before);
+            cudaError_t e1 = launch_rebuild(s);
+            if (e1 == cudaSuccess) e1 = launch_integrate_gated(s);
+            if (e1 == cudaSuccess) e1 = launch_cover_check(s);
+            if (e1 == cudaSuccess) e1 = launch_forces(s, false);
+            if (e1 == cudaSuccess) e1 = launch_project(s, true);
+            b->kernels_per_rebuild[k] = (int)(s->launches - before);
             s->launches = before;
             s->stream = keep;
             s->prof_on = prof;
@@ -275,7 +263,7 @@ int capture(qhp_batch_s* b) {
             fail(e2, "batch body capture end");
         }
         if (rc == QHP_OK)
-            fail(cudaStreamUpdateCaptureDependencies(b->stream, conds.data(), nullptr, 2 * n,
+            fail(cudaStreamUpdateCaptureDependencies(b->stream, conds.data(), nullptr, n,
                                                      cudaStreamSetCaptureDependencies),
                  "batch join");
     }
@@ -590,10 +578,10 @@ int qhp_batch_get_info(qhp_batch b, qhp_batch_info* out) {
     cudaStreamSynchronize(b->stream);
     int64_t extra = 0;
     for (size_t k = 0; k < b->sys.size() && k < b->kernels_per_rebuild.size(); ++k) {
-        unsigned rb[3] = {0u, 0u, 0u};
+        unsigned rb[2] = {0u, 0u};
         cudaMemcpy(rb, b->sys[k]->rebuild_count, sizeof rb, cudaMemcpyDeviceToHost);
         out->rebuilds += rb[0];
-        extra += (int64_t)rb[1] * b->kernels_per_rebuild[k] + (int64_t)rb[2] * b->kernels_per_early[k];
+        extra += (int64_t)rb[1] * b->kernels_per_rebuild[k];
     }
     out->kernel_launches = b->launches + extra;
     return QHP_OK;

@@ -175,11 +175,10 @@ int enqueue_respa_forces(qhp_system_s* s, bool force_rebuild) {
     return QHP_OK;
 }
 
-// While a step graph is being captured: add an IF node driven by k_check and capture a
-// rebuild chain into its body on the auxiliary stream, so steps without a rebuild launch none
-// of those kernels.  early = false: the rebuild before this step's forces (cells, sort, list,
-// positions); early = true: the end-of-step rebuild for the next step (launch_early_rebuild).
-int enqueue_rebuild_conditional(qhp_system_s* s, bool early = false) {
+// While a step graph is being captured: add an IF node driven by k_check and capture the
+// list rebuild chain (cells, sort, list, positions) into its body on the auxiliary stream,
+// so steps without a rebuild launch none of those kernels.
+int enqueue_rebuild_conditional(qhp_system_s* s) {
     cudaStreamCaptureStatus st;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -190,7 +189,7 @@ int enqueue_rebuild_conditional(qhp_system_s* s, bool early = false) {
     memset(pbuf, 0, sizeof pbuf);   // the struct holds a union without a default constructor
     cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(pbuf);
     p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = early ? s->early_handle : s->cond_handle;
+    p.conditional.handle = s->cond_handle;
     p.conditional.type = cudaGraphCondTypeIf;
     p.conditional.size = 1;
     cudaGraphNode_t node;
@@ -201,16 +200,11 @@ int enqueue_rebuild_conditional(qhp_system_s* s, bool early = false) {
     cudaStream_t main = s->stream;
     s->stream = s->aux_stream;
     const int64_t before = s->launches;
-    cudaError_t e = cudaSuccess;
-    if (early) {
-        e = launch_early_rebuild(s);
-    } else {
-        e = launch_rebuild(s);
-        if (e == cudaSuccess) e = launch_integrate_gated(s);
-        if (e == cudaSuccess && s->respa_n) e = launch_contract(s, true);
-        if (e == cudaSuccess) e = launch_cover_check(s);
-    }
-    (early ? s->kernels_per_early : s->kernels_per_rebuild) = s->launches - before;
+    cudaError_t e = launch_rebuild(s);
+    if (e == cudaSuccess) e = launch_integrate_gated(s);
+    if (e == cudaSuccess && s->respa_n) e = launch_contract(s, true);
+    if (e == cudaSuccess) e = launch_cover_check(s);
+    s->kernels_per_rebuild = s->launches - before;
     s->stream = main;
     cudaGraph_t out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s->aux_stream, &out);
@@ -227,10 +221,7 @@ int capture_step_graph(qhp_system_s* s, bool adqtb) {
     if (!s->aux_stream) QHP_CUDA(cudaStreamCreateWithFlags(&s->aux_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     QHP_CUDA(cudaGraphCreate(&g, 0));
-    const bool early = !(s->respa_n && !adqtb);   // plain steps end with the early-rebuild node
     cudaError_t e = cudaGraphConditionalHandleCreate(&s->cond_handle, g, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess && early)
-        e = cudaGraphConditionalHandleCreate(&s->early_handle, g, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess)
         e = cudaStreamBeginCaptureToGraph(s->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
@@ -239,19 +230,16 @@ int capture_step_graph(qhp_system_s* s, bool adqtb) {
     }
     const int64_t before = s->launches;
     s->cond_active = 1;
-    s->early_active = early ? 1 : 0;
     s->kernels_per_rebuild = 0;
-    s->kernels_per_early = 0;
     const int rc = enqueue_step(s, adqtb);
     s->cond_active = 0;
-    s->early_active = 0;
     cudaGraph_t g2 = nullptr;
     e = cudaStreamEndCapture(s->stream, &g2);
     if (rc != QHP_OK || e != cudaSuccess) {
         cudaGraphDestroy(g);
         return rc != QHP_OK ? rc : cuda_fail(e, "step graph capture end");
     }
-    s->kernels_per_step = s->launches - before - s->kernels_per_rebuild - s->kernels_per_early;
+    s->kernels_per_step = s->launches - before - s->kernels_per_rebuild;
     s->launches = before;
     e = cudaGraphInstantiate(&s->graph_exec, g, 0);
     cudaGraphDestroy(g);
@@ -322,11 +310,6 @@ int enqueue_step(qhp_system_s* s, bool adqtb) {
     if (prof) QHP_CUDA(record_stage(s, 4));
     QHP_CUDA(launch_project(s, true));
     if (prof) QHP_CUDA(record_stage(s, 5));
-    // the list the check marked for renewal is rebuilt from the centroids the next step
-    // starts from (outside the stage records)
-    if (s->cond_active) TRY(enqueue_rebuild_conditional(s, true));
-    else QHP_CUDA(launch_early_rebuild(s));
-    if (prof) QHP_CUDA(record_stage(s, 6));
     return QHP_OK;
 }
 
@@ -581,7 +564,7 @@ int qhp_destroy_system(qhp_sys s) {
     free_all(s);
     if (s->status_event) cudaEventDestroy(s->status_event);
     if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
-    for (int k = 0; k < 7; ++k)
+    for (int k = 0; k < 6; ++k)
         if (s->prof_ev[k]) cudaEventDestroy(s->prof_ev[k]);
     if (s->status_host) cudaFreeHost(s->status_host);
     if (s->own_stream) cudaStreamDestroy(s->own_stream);
@@ -685,10 +668,9 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     TRY(dalloc(s, &s->est_part, (size_t)3 * (N + 1)));
     TRY(dalloc(s, &s->status, 1));
     TRY(dalloc(s, &s->dev_max, 1));
-    TRY(dalloc(s, &s->rebuild_flag, 2));
-    TRY(dalloc(s, &s->dev_prev, 1));
+    TRY(dalloc(s, &s->rebuild_flag, 1));
     TRY(dalloc(s, &s->step_ctr, 1));
-    TRY(dalloc(s, &s->rebuild_count, 4));   // [0] all rebuilds; inside step graphs: [1] now, [2] end of step
+    TRY(dalloc(s, &s->rebuild_count, 2));   // [0] all rebuilds, [1] those run inside step graphs
     TRY(dalloc(s, &s->Tmat, (size_t)P * P));
     TRY(dalloc(s, &s->Tproj, (size_t)P * P));
     TRY(dalloc(s, &s->Tmat_f, (size_t)P * P));
@@ -711,9 +693,7 @@ int qhp_set_beads(qhp_sys s, int P, double temperature, uint64_t seed) {
     QHP_CUDA(cudaMemset(s->status, 0, sizeof(unsigned)));
     QHP_CUDA(cudaMemset(s->dev_max, 0, sizeof(unsigned)));
     QHP_CUDA(cudaMemset(s->step_ctr, 0, sizeof(unsigned long long)));
-    QHP_CUDA(cudaMemset(s->rebuild_count, 0, 4 * sizeof(unsigned)));
-    QHP_CUDA(cudaMemset(s->rebuild_flag, 0, 2 * sizeof(int)));
-    QHP_CUDA(cudaMemset(s->dev_prev, 0, sizeof(unsigned)));
+    QHP_CUDA(cudaMemset(s->rebuild_count, 0, 2 * sizeof(unsigned)));
     QHP_CUDA(cudaMemset(s->fmode, 0, sizeof(double) * NP3));
     TRY(upload_matrices(s));
     if (s->th.kind == QHP_THERMO_ADQTB && P != 1) s->th.kind = QHP_THERMO_PILE;
@@ -1033,18 +1013,16 @@ int qhp_get_info(qhp_sys s, qhp_info* out) {
     out->n_cells_per_edge = s->n_c;
     if (s->beads_set) {
         cudaStreamSynchronize(s->stream);
-        unsigned rb[4] = {0u, 0u, 0u, 0u};
+        unsigned rb[2] = {0u, 0u};
         std::vector<int> cnt(s->N);
         cudaMemcpy(rb, s->rebuild_count, sizeof rb, cudaMemcpyDeviceToHost);
         cudaMemcpy(cnt.data(), s->nbr_count, sizeof(int) * s->N, cudaMemcpyDeviceToHost);
         int64_t tot = 0;
         for (int v : cnt) tot += v;
         out->rebuilds = rb[0];
-        out->early_rebuilds = (int)rb[3];
         out->list_entries = tot;
         // kernels run inside step-graph conditionals are counted by the device
-        out->kernel_launches =
-            s->launches + (int64_t)rb[1] * s->kernels_per_rebuild + (int64_t)rb[2] * s->kernels_per_early;
+        out->kernel_launches = s->launches + (int64_t)rb[1] * s->kernels_per_rebuild;
     }
     return QHP_OK;
 }
@@ -1107,23 +1085,20 @@ int qhp_get_qtb_records(qhp_sys s, float* v, float* F) {
 }
 
 // Blob: header, Q, Pm, list anchors, [adQTB: gamma, RATIO averages, u, v, F].  The
-// anchors (centroids at the last list build), the running deviation maximum and its value
-// at the previous check (the early-rebuild estimate) are part of the state: the mixed path
-// rounds positions relative to the anchors and the next rebuild depends on both maxima, so a
-// restore that rebuilt from fresh anchors would not continue bit for bit.
+// anchors (centroids at the last list build) and the running deviation maximum are
+// part of the state: the mixed path rounds positions relative to the anchors and the
+// next rebuild depends on the maximum, so a restore that rebuilt from fresh anchors
+// would not continue bit for bit.
 struct StateHeader {
-    uint64_t magic, N, P, step, n_seg, ratio_first, precision, dev_max_bits, dev_prev_bits, forces_kind;
+    uint64_t magic, N, P, step, n_seg, ratio_first, precision, dev_max_bits;
 };
-static const uint64_t STATE_MAGIC = 0x3350485153544154ull;
+static const uint64_t STATE_MAGIC = 0x3250485153544154ull;
 
-// The projected forces the next B kick uses are stored too (and, for RESPA, the slow ones):
-// an end-of-step list rebuild renews the list after they were computed, and forces summed
-// over the new list would differ in their last bits.
 static size_t state_bytes(const qhp_system_s* s) {
     const size_t NP3 = (size_t)s->N * 3 * s->P;
     const size_t nq = s->qtb_u ? (size_t)s->n_seg * 3 * s->N : 0;
     const size_t ng = s->qtb_u ? 2 * (size_t)(s->n_seg + 1) : 0;
-    return sizeof(StateHeader) + (4 * NP3 + 3 * (size_t)s->N) * sizeof(double) + 3 * ng * sizeof(double) +
+    return sizeof(StateHeader) + (2 * NP3 + 3 * (size_t)s->N) * sizeof(double) + 3 * ng * sizeof(double) +
            3 * nq * sizeof(float);
 }
 
@@ -1146,23 +1121,16 @@ int qhp_get_state(qhp_sys s, void* buf, size_t* size) {
     }
     if (!s->forces_valid) TRY(qhp_compute_forces(s));
     TRY(sync_and_check(s));
-    unsigned dm = 0, dp = 0;
+    unsigned dm = 0;
     QHP_CUDA(cudaMemcpy(&dm, s->dev_max, sizeof dm, cudaMemcpyDeviceToHost));
-    QHP_CUDA(cudaMemcpy(&dp, s->dev_prev, sizeof dp, cudaMemcpyDeviceToHost));
     char* p = static_cast<char*>(buf);
     StateHeader h{STATE_MAGIC, (uint64_t)s->N, (uint64_t)s->P, (uint64_t)s->step, (uint64_t)(s->qtb_u ? s->n_seg : 0),
-                  (uint64_t)s->qtb_ratio_first, (uint64_t)s->precision, (uint64_t)dm, (uint64_t)dp,
-                  (uint64_t)s->forces_kind};
+                  (uint64_t)s->qtb_ratio_first, (uint64_t)s->precision, (uint64_t)dm};
     memcpy(p, &h, sizeof h);
     p += sizeof h;
     QHP_CUDA(cudaMemcpy(p, s->Q, NP3 * sizeof(double), cudaMemcpyDeviceToHost));
     p += NP3 * sizeof(double);
     QHP_CUDA(cudaMemcpy(p, s->Pm, NP3 * sizeof(double), cudaMemcpyDeviceToHost));
-    p += NP3 * sizeof(double);
-    QHP_CUDA(cudaMemcpy(p, s->fmode, NP3 * sizeof(double), cudaMemcpyDeviceToHost));
-    p += NP3 * sizeof(double);
-    if (s->forces_kind == 1) QHP_CUDA(cudaMemcpy(p, s->fmode_s, NP3 * sizeof(double), cudaMemcpyDeviceToHost));
-    else memset(p, 0, NP3 * sizeof(double));
     p += NP3 * sizeof(double);
     QHP_CUDA(cudaMemcpy(p, s->anchor, 3 * (size_t)s->N * sizeof(double), cudaMemcpyDeviceToHost));
     p += 3 * (size_t)s->N * sizeof(double);
@@ -1207,8 +1175,6 @@ int qhp_set_state(qhp_sys s, const void* buf, size_t size) {
     p += NP3 * sizeof(double);
     QHP_CUDA(cudaMemcpy(s->Pm, p, NP3 * sizeof(double), cudaMemcpyHostToDevice));
     p += NP3 * sizeof(double);
-    const char* fm = p;   // the stored projected forces, copied in after the rebuild below
-    p += 2 * NP3 * sizeof(double);
     QHP_CUDA(cudaMemcpy(s->anchor, p, 3 * (size_t)s->N * sizeof(double), cudaMemcpyHostToDevice));
     p += 3 * (size_t)s->N * sizeof(double);
     if (nq) {
@@ -1226,23 +1192,14 @@ int qhp_set_state(qhp_sys s, const void* buf, size_t size) {
     s->step = (int64_t)h.step;
     unsigned long long st = h.step;
     QHP_CUDA(cudaMemcpy(s->step_ctr, &st, sizeof st, cudaMemcpyHostToDevice));
-    // rebuild the list from the stored anchors and the positions, then the stored forces
-    if (h.forces_kind == 1 && !(s->respa_n && s->fmode_s)) {
-        set_error("state blob holds RESPA forces; set the same RESPA splitting first");
-        return QHP_ERR_ARG;
-    }
+    // rebuild the list from the stored anchors, then the forces at the restored modes
     s->keep_anchor = 1;
     int rc = ensure_capacity(s);
-    if (rc == QHP_OK) rc = h.forces_kind == 1 ? enqueue_respa_forces(s, true) : enqueue_forces(s, true, false);
+    if (rc == QHP_OK) rc = enqueue_forces(s, true, false);
     s->keep_anchor = 0;
     TRY(rc);
-    QHP_CUDA(cudaStreamSynchronize(s->stream));
-    QHP_CUDA(cudaMemcpy(s->fmode, fm, NP3 * sizeof(double), cudaMemcpyHostToDevice));
-    if (h.forces_kind == 1) QHP_CUDA(cudaMemcpy(s->fmode_s, fm + NP3 * sizeof(double), NP3 * sizeof(double),
-                                                cudaMemcpyHostToDevice));
-    const unsigned dm = (unsigned)h.dev_max_bits, dp = (unsigned)h.dev_prev_bits;
+    const unsigned dm = (unsigned)h.dev_max_bits;
     QHP_CUDA(cudaMemcpyAsync(s->dev_max, &dm, sizeof dm, cudaMemcpyHostToDevice, s->stream));
-    QHP_CUDA(cudaMemcpyAsync(s->dev_prev, &dp, sizeof dp, cudaMemcpyHostToDevice, s->stream));
     s->forces_valid = true;
     s->list_valid = true;
     return sync_and_check(s);
@@ -1256,7 +1213,7 @@ extern "C" {
 int qhp_set_profiling(qhp_sys s, int on) {
     if (!s) return QHP_ERR_ARG;
     if (on && !s->prof_ev[0])
-        for (int k = 0; k < 7; ++k) QHP_CUDA(cudaEventCreate(&s->prof_ev[k]));
+        for (int k = 0; k < 6; ++k) QHP_CUDA(cudaEventCreate(&s->prof_ev[k]));
     if ((on != 0) != (s->prof_on != 0)) invalidate_graph(s);   // events are captured into the step graph
     s->prof_on = on ? 1 : 0;
     return QHP_OK;
@@ -1287,13 +1244,7 @@ int qhp_get_profile(qhp_sys s, qhp_profile* out) {
     out->bonded_ms = t[3];
     out->project_ms = t[4];
     float tot = 0.f;
-    const int last = s->respa_n ? 5 : 6;   // plain steps end with the end-of-step rebuild node
-    QHP_CUDA(cudaEventElapsedTime(&tot, s->prof_ev[0], s->prof_ev[last]));
-    if (last == 6) {
-        float te = 0.f;
-        QHP_CUDA(cudaEventElapsedTime(&te, s->prof_ev[5], s->prof_ev[6]));
-        out->list_ms += te;   // both rebuild chains
-    }
+    QHP_CUDA(cudaEventElapsedTime(&tot, s->prof_ev[0], s->prof_ev[5]));
     out->step_ms = tot;
     return QHP_OK;
 }

@@ -298,9 +298,9 @@ static IntegrateArgs make_iargs_batch(qhp_system_s* s) {
     return A;
 }
 
-cudaError_t launch_integrate_gated(qhp_system_s* s, const int* gate) {
+cudaError_t launch_integrate_gated(qhp_system_s* s) {
     IntegrateArgs A = make_iargs(s);
-    A.gate = gate ? gate : s->rebuild_flag;
+    A.gate = s->rebuild_flag;
     const int nb = (s->N + A.apb - 1) / A.apb;
     const bool mixed = s->precision == QHP_MIXED;
     const size_t sm = integrate_smem(s->P, mixed);

@@ -61,39 +61,28 @@ __device__ __forceinline__ int cell_coord(double C, double L, int n_c, double* f
     return c < n_c - 1 ? c : n_c - 1;
 }
 
-// Decide whether the list must be rebuilt now or at the end of the step (list_check_decide).
-// Inside a step graph the decisions drive the conditional nodes of the two rebuild chains.
-__global__ void k_check(unsigned* dev_max, unsigned* dev_prev, float half_skin, int* flag, int force,
-                        unsigned* rebuild_count, cudaGraphConditionalHandle cond, int use_cond,
-                        cudaGraphConditionalHandle early, int use_early) {
-    const int r = list_check_decide(dev_max, dev_prev, half_skin, force, flag, rebuild_count);
+// Decide whether the list must be rebuilt; clear the deviation maximum if so.  Inside a
+// step graph the decision also drives the conditional node that holds the rebuild chain.
+__global__ void k_check(unsigned* dev_max, float thr2, int* flag, int force, unsigned* rebuild_count,
+                        cudaGraphConditionalHandle cond, int use_cond) {
+    const float dmax = __uint_as_float(*dev_max);
+    const int rebuild = force || !(dmax <= thr2);   // NaN also triggers a rebuild
+    *flag = rebuild;
+    if (rebuild) {
+        *dev_max = 0u;
+        *rebuild_count += 1u;
+    }
     if (use_cond) {
-        cudaGraphSetConditional(cond, (r & 1) ? 1u : 0u);
-        if (r & 1) rebuild_count[1] += 1u;   // rebuild chains run inside the step graph
+        cudaGraphSetConditional(cond, rebuild ? 1u : 0u);
+        if (rebuild) rebuild_count[1] += 1u;   // rebuild chains run inside the step graph
     }
-    if (use_early) {
-        cudaGraphSetConditional(early, (r & 2) ? 1u : 0u);
-        if (r & 2) rebuild_count[2] += 1u;
-    }
-}
-
-// Start of the end-of-step rebuild: the new anchors restart the deviation maximum.
-__global__ void k_early_begin(const int* gate, unsigned* dev_max, unsigned* rebuild_count) {
-    if (!*gate) return;
-    *dev_max = 0u;
-    rebuild_count[0] += 1u;
-    rebuild_count[3] += 1u;
 }
 
 // Right after a rebuild the deviation maximum is measured from the new anchors; the list
 // covers every bead pair within rc only if no bead lies farther than skin/2 from its anchor.
-// The maximum is kept as the next check's reference for its growth; clear lowers the gate.
-__global__ void k_check_cover(int* gate, const unsigned* dev_max, float thr2, unsigned* status, unsigned* dev_prev,
-                              int clear) {
-    if (!*gate) return;
+__global__ void k_check_cover(const int* flag, const unsigned* dev_max, float thr2, unsigned* status) {
+    if (!*flag) return;
     if (!(__uint_as_float(*dev_max) <= thr2)) atomicOr(status, ST_SPREAD);
-    *dev_prev = *dev_max;
-    if (clear) *gate = 0;
 }
 
 __global__ void k_zero_ints(const int* flag, int* a, int n) {
@@ -561,34 +550,23 @@ int list_sort_prepare(qhp_system_s* s) {
 cudaError_t launch_list_check(qhp_system_s* s, bool force) {
     const float half = (float)(0.5 * s->ff.skin);
     s->launches++;
-    k_check<<<1, 1, 0, s->stream>>>(s->dev_max, s->dev_prev, half, s->rebuild_flag, force ? 1 : 0, s->rebuild_count,
-                                    s->cond_handle, s->cond_active, s->early_handle, s->early_active);
+    k_check<<<1, 1, 0, s->stream>>>(s->dev_max, half * half, s->rebuild_flag, force ? 1 : 0, s->rebuild_count,
+                                    s->cond_handle, s->cond_active);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cover_check(qhp_system_s* s, int* gate, bool clear) {
+cudaError_t launch_cover_check(qhp_system_s* s) {
     const float half = (float)(0.5 * s->ff.skin);
     s->launches++;
-    k_check_cover<<<1, 1, 0, s->stream>>>(gate ? gate : s->rebuild_flag, s->dev_max, half * half, s->status,
-                                          s->dev_prev, clear ? 1 : 0);
+    k_check_cover<<<1, 1, 0, s->stream>>>(s->rebuild_flag, s->dev_max, half * half, s->status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_early_rebuild(qhp_system_s* s) {
-    int* gate = s->rebuild_flag + 1;
-    s->launches++;
-    k_early_begin<<<1, 1, 0, s->stream>>>(gate, s->dev_max, s->rebuild_count);
-    cudaError_t e = launch_rebuild(s, gate);
-    if (e == cudaSuccess) e = launch_integrate_gated(s, gate);
-    if (e == cudaSuccess) e = launch_cover_check(s, gate, true);
-    return e == cudaSuccess ? cudaGetLastError() : e;
-}
-
-cudaError_t launch_rebuild(qhp_system_s* s, const int* gate) {
+cudaError_t launch_rebuild(qhp_system_s* s) {
     const int N = s->N;
     const int tb = 256, gN = (N + tb - 1) / tb;
     const int ncell = s->n_c * s->n_c * s->n_c;
-    const int* flag = gate ? gate : s->rebuild_flag;
+    const int* flag = s->rebuild_flag;
     cudaStream_t st = s->stream;
     if (s->list_mode) {
         k_zero_ints<<<(ncell + tb - 1) / tb, tb, 0, st>>>(flag, s->cell_count, ncell);

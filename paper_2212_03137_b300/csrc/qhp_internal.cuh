@@ -57,32 +57,6 @@ __device__ __forceinline__ bool qhp_in_bounds(long long i, long long n, const un
 #define QHP_IN_BOUNDS(i, n, status) true
 #endif
 
-// The list check of one system (single-system k_check and the batched step's check alike).
-// hard: some bead lies farther than skin/2 from its anchor (or a rebuild is forced): the list
-// no longer covers every pair within rc and is rebuilt before this step's forces.  soft: the
-// deviation maximum, grown for two more steps at the last step's rate, would pass skin/2: the
-// list is rebuilt at the end of this step, from the centroids the next step starts from, so
-// that rebuilds rarely interrupt a step.  Returns hard | soft << 1.
-__device__ __forceinline__ int list_check_decide(unsigned* dev_max, unsigned* dev_prev, float half_skin, int force,
-                                                 int* flag, unsigned* rebuild_count) {
-    const unsigned dbits = atomicAdd(dev_max, 0u);   // coherent read of the blocks' maxima
-    const float dmax = __uint_as_float(dbits);
-    const int hard = force || !(dmax <= half_skin * half_skin);   // NaN also triggers a rebuild
-    int soft = 0;
-    if (!hard) {
-        const float d = sqrtf(dmax), d0 = sqrtf(__uint_as_float(*dev_prev));
-        soft = d + 2.0f * fmaxf(d - d0, 0.0f) > half_skin;
-        *dev_prev = dbits;
-    }
-    flag[0] = hard;
-    flag[1] = soft;
-    if (hard) {
-        *dev_max = 0u;
-        rebuild_count[0] += 1u;
-    }
-    return hard | (soft << 1);
-}
-
 // Philox4x32-10 counter tags (same definition as the oracle, written independently).
 enum : uint32_t { TAG_INIT_Q = 1, TAG_INIT_P = 2, TAG_OSTEP = 3, TAG_QTB_WHITE = 4 };
 
@@ -283,8 +257,7 @@ struct qhp_system_s {
     unsigned* dev_max = nullptr;                             // max squared deviation (float bits)
     float* dev_atom = nullptr;     // mixed: per sorted atom, max over beads of |x_ib - A_i|^2 this step
     float* dev_atom_c = nullptr;   // the same over the contracted beads (RESPA)
-    int* rebuild_flag = nullptr;   // [0] rebuild now (the list no longer covers), [1] rebuild at the end of the step
-    unsigned* dev_prev = nullptr;  // the deviation maximum at the previous check (float bits)
+    int* rebuild_flag = nullptr;
     unsigned long long* step_ctr = nullptr;                  // device copy of the step counter
     int64_t rebuilds_host = 0;
     int keep_anchor = 0;           // 1 while a checkpoint restore rebuilds from stored anchors
@@ -302,12 +275,9 @@ struct qhp_system_s {
     int prof_on = 0;               // per-stage events recorded inside each step
     int use_graphs = 1;            // 0: launch each step's kernels directly
     cudaGraphConditionalHandle cond_handle = 0;   // IF node around the rebuild chain of the step graph
-    cudaGraphConditionalHandle early_handle = 0;  // IF node around the early rebuild at the end of the step
-    int early_active = 0;                         // the step graph being captured holds early_handle
-    int64_t kernels_per_early = 0;
     int cond_active = 0;           // 1 while capturing a step graph that uses it
     cudaStream_t aux_stream = nullptr;            // captures the conditional body
-    cudaEvent_t prof_ev[7] = {};   // stage boundaries; [6] after the end-of-step rebuild node
+    cudaEvent_t prof_ev[6] = {};
     double* cent_buf = nullptr;    // [N][3] centroid gather buffer
     unsigned* rebuild_count = nullptr;
 
@@ -401,17 +371,12 @@ struct StepArgs;
 
 cudaError_t launch_init_modes(qhp_system_s* s);
 cudaError_t launch_integrate(qhp_system_s* s, bool integrate, bool adqtb);
-cudaError_t launch_integrate_gated(qhp_system_s* s, const int* gate = nullptr);   // positions only, if *gate (default: the rebuild flag)
+cudaError_t launch_integrate_gated(qhp_system_s* s);   // positions only, if the rebuild flag is set
 int qtb_setup(qhp_system_s* s);
 cudaError_t launch_project(qhp_system_s* s, bool kick);
 cudaError_t launch_list_check(qhp_system_s* s, bool force);
-cudaError_t launch_rebuild(qhp_system_s* s, const int* gate = nullptr);   // runs if *gate (default: the rebuild flag)
-// after a rebuild: every bead within skin/2; records the deviation maximum for the next
-// check's growth estimate and, with clear, lowers the gate
-cudaError_t launch_cover_check(qhp_system_s* s, int* gate = nullptr, bool clear = false);
-// the early rebuild at the end of a step the check marked (flag [1]): list from the current
-// centroids for the next step, positions, cover check
-cudaError_t launch_early_rebuild(qhp_system_s* s);
+cudaError_t launch_rebuild(qhp_system_s* s);
+cudaError_t launch_cover_check(qhp_system_s* s);   // after a rebuild: every bead within skin/2
 cudaError_t launch_integrate_respa(qhp_system_s* s, double ws);   // B (fast + ws x slow) A O A
 cudaError_t launch_contract(qhp_system_s* s, bool gated);        // contracted bead positions
 cudaError_t launch_project_contracted(qhp_system_s* s, bool kick);
@@ -464,12 +429,10 @@ int batch_stage_force(const std::vector<qhp_system_s*>& v, BatchStage& st, int* 
 // that completes the system's last integrate item.
 struct CheckArgs {
     unsigned* dev_max;
-    unsigned* dev_prev;
-    int* flag;                        // [0] rebuild now, [1] rebuild at the end of the step
+    int* flag;
     unsigned* rebuild_count;
-    cudaGraphConditionalHandle cond;  // the rebuild-now node (the system's step finishes there)
-    cudaGraphConditionalHandle early; // the end-of-step rebuild node
-    float half_skin;
+    cudaGraphConditionalHandle cond;
+    float thr2;
 };
 // Device state of the step's grid barriers: [0] arrivals, [1] generation, [2] finished blocks.
 struct StepBatchState {

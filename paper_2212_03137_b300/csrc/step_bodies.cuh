@@ -224,12 +224,15 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& A, int bx, u
 }
 
 __device__ __forceinline__ void batch_check(const CheckArgs& a) {
-    __threadfence();   // the blocks' deviation maxima are visible before they are read
-    const int r = list_check_decide(a.dev_max, a.dev_prev, a.half_skin, 0, a.flag, a.rebuild_count);
-    if (r & 1) a.rebuild_count[1] += 1u;   // rebuild chains run inside the step graph
-    if (r & 2) a.rebuild_count[2] += 1u;
-    cudaGraphSetConditional(a.cond, (r & 1) ? 1u : 0u);
-    cudaGraphSetConditional(a.early, (r & 2) ? 1u : 0u);
+    const float dmax = __uint_as_float(atomicAdd(a.dev_max, 0u));   // coherent read of the blocks' maxima
+    const int rebuild = !(dmax <= a.thr2);                          // NaN also triggers a rebuild
+    *a.flag = rebuild;
+    if (rebuild) {
+        *a.dev_max = 0u;
+        a.rebuild_count[0] += 1u;
+        a.rebuild_count[1] += 1u;
+    }
+    cudaGraphSetConditional(a.cond, rebuild ? 1u : 0u);
 }
 
 struct ProjectArgs {

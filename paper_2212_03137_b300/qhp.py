@@ -52,7 +52,7 @@ class qhp_info(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("P", C.c_int), ("precision", C.c_int), ("list_mode", C.c_int),
                 ("step", C.c_int64), ("rebuilds", C.c_int64), ("list_entries", C.c_int64),
                 ("list_capacity", C.c_int64), ("kernel_launches", C.c_int64),
-                ("n_cells_per_edge", C.c_int), ("early_rebuilds", C.c_int)]
+                ("n_cells_per_edge", C.c_int), ("reserved", C.c_int)]
 
 
 _lib = None

@@ -57,10 +57,6 @@ def test_batch_equals_single_systems_bitwise():
             assert qhp.qhp_get_info(s.h).rebuilds == qhp.qhp_get_info(m.h).rebuilds
             assert qhp.qhp_get_info(m.h).step == 25
         assert info.rebuilds > len(MIX)
-        # besides each system's initial build, most rebuilds run at the end of a step (growth
-        # estimate), not inside one
-        early = sum(qhp.qhp_get_info(m.h).early_rebuilds for m in members)
-        assert early > (info.rebuilds - len(MIX)) // 2, (early, info.rebuilds)
         pr = qhp.qhp_batch_get_profile(b.h)
         assert pr.pair_ms > 0 and pr.step_ms > pr.pair_ms
     # the members work on their own again after the batch is gone
