@@ -429,7 +429,7 @@ def run_ours(args, ws, rank, local):
         if rank == 0:
             out["e2e"] = e2e
     if args.fp64 and rank == 0:
-        out["fp64_gpu_path"] = _fp64_path(args, cfg, dev)
+        out["fp64_gpu_path"] = _fp64_path(args, cfg, dev, flops_launch, n_sm, smax)
         out["speedup_vs_fp64_gpu_path"] = value / ws / out["fp64_gpu_path"]["value"]
     if rank == 0 and args.workload == "grad_216w":
         out["gradient"] = _time_gradient(qhp, h, cfg, N, P)
@@ -647,28 +647,38 @@ def _e2e(args, h, N, P, step, dev, ws, inner=1):
             "d2h_bytes_per_step": int(Pm.nbytes + cent.nbytes)}
 
 
-def _fp64_path(args, cfg, dev):
-    """The same workload on the plain FP64 GPU path (FP64 pair math, FP64 forces)."""
+def _fp64_path(args, cfg, dev, flops=None, n_sm=None, smax=None):
+    """The same workload on the plain FP64 GPU path (FP64 pair math, FP64 forces), with the FP64
+    pair kernel's own fraction of the FP64 peak (the same algorithmic flops per launch)."""
     import torch
     from paper_2212_03137_b300 import qhp
     s = qhp.System.from_config(cfg, precision="fp64")
     stream = torch.cuda.current_stream(dev)
     assert stream.cuda_stream != 0, "timing needs an explicit stream"
     qhp.qhp_set_stream(s.h, stream.cuda_stream)
+    qhp.qhp_set_profiling(s.h, True)
     step = qhp.qhp_step_adqtb if cfg.thermostat == "adqtb" else qhp.qhp_step_rpmd
     step(s.h, 1)
     qhp.qhp_sync(s.h)
     k = max(2, min(args.steps, 5))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tot = 0.0
+    tot, pair = 0.0, []
     for _ in range(k):
         e0.record(stream)
         step(s.h, 1)
         e1.record(stream)
         e1.synchronize()
         tot += e0.elapsed_time(e1)
+        pair.append(qhp.qhp_get_profile(s.h).pair_ms)
     s.close()
-    return {"value": s.n_atoms * s.P * k / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / k, "steps": k}
+    out = {"value": s.n_atoms * s.P * k / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / k, "steps": k}
+    if flops and n_sm and smax and min(pair) > 0:
+        peak = n_sm * 2 * 2 * smax * 1e6 / 1e12   # FP64: 2 FMA lanes per SM on this part
+        achieved = flops / (float(np.mean(pair)) * 1e-3) / 1e12
+        out["pair_roofline"] = {"kernel": "FP64 pair kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                                "unit": "TFLOP/s", "frac": achieved / peak, "mean_launch_ms": float(np.mean(pair)),
+                                "peak_source": f"FP64 FMA: {n_sm} SMs x 2 lanes x 2 x {smax:.0f} MHz"}
+    return out
 
 
 def _oracle_sample(cfg, n_beads):
