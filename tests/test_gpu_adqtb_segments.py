@@ -7,7 +7,8 @@ per-type FDT deviation (Eq. (21), averaged over the type's dofs, Sec. III.B.2), 
 segment, which isolates the end-of-segment kernels from the trajectory:
 - the spectra kernel is specialised on n_seg (bins per thread 1, 2, 3 and 5 for n_seg = 256,
   512, 1024 and 2048), so each of those runs once on a 64-water box;
-- the 8,000-water box runs the config-3 segment length (1024) with all 72,000 dofs averaged.
+- the 8,000-water box runs the 72,000-water workload's segment length (1024) with all 72,000 dofs
+  averaged.
 
 Tolerances: the records and FFTs are FP32 (~1e-6 relative after an FFT of a few thousand
 points) and the per-type sums FP64.  Delta_bar is a difference of two spectra of scale
